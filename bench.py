@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the bit-vectorized octahedron-model SCA on one GB300 (or N independent replicas).
+
+Workload (one "step"): an L = 65536 periodic lattice (4.3 G sites, 1 GiB of packed slopes),
+flat start, p = 1, q = 0, 1024 Monte-Carlo steps with the exact roughness W^2 observed at
+MCS 1, 2, 4, ..., 1024.  Metric: site updates per second (L^2 attempts per MCS).  The state
+(1 GiB, read and written every MCS) is far larger than L2, so no flush is needed between steps.
+
+Arms:
+  default          the CUDA library through its C ABI, state resident in HBM;
+  --impl reference the CPU oracle (test infrastructure, deliberately slow) on a bounded sample
+                   of the same workload, on the host's cores.
+
+With torchrun (WORLD_SIZE > 1) every rank runs its own replica on its own GPU (the update has no
+exchange between independent lattices); value = all ranks' updates / max-over-ranks time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site updates/s"
+UNIT = "updates/s"
+WORKLOAD = "octahedron SCA L=65536 p=1 q=0 flat, 1024 MCS, exact W^2 at 2^0..2^10"
+BYTES_PER_UPDATE = 0.5   # each slope bit read once and written once per MCS (roofline unit)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=65536)
+    ap.add_argument("--p", type=float, default=1.0)
+    ap.add_argument("--q", type=float, default=0.0)
+    ap.add_argument("--mcs", type=int, default=1024)
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 two-pass, 2 fused")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the p=1/2 context line")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def obs_times(mcs):
+    t, out = 1, []
+    while t < mcs:
+        out.append(t)
+        t *= 2
+    out.append(mcs)
+    return out
+
+
+def config(a, world):
+    return {"workload": WORKLOAD if (a.L, a.p, a.q, a.mcs) == (65536, 1.0, 0.0, 1024) else
+            "octahedron SCA L=%d p=%g q=%g flat, %d MCS, exact W^2 at log times"
+            % (a.L, a.p, a.q, a.mcs),
+            "L": a.L, "p": a.p, "q": a.q, "mcs_per_step": a.mcs,
+            "observations": len(obs_times(a.mcs)),
+            "state_bytes": a.L * a.L // 4,
+            "l2_policy": "state (%.2f GiB) exceeds L2 (129 MB); no flush needed"
+                         % (a.L * a.L / 4 / 2 ** 30),
+            "parallelism": "replicas x%d" % world}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- roofline inputs
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("sca_update.cu", "sca_fused.cu", "sca_rng.cuh", "sca_internal.h"):
+        with open(os.path.join(ROOT, "paper_1606_00310_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel_name, L):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel_name)
+    if not e or e.get("src_sha256") != kernel_source_hash():
+        return None
+    return float(e["bytes_per_launch_at_L"][str(L)]) if str(L) in e.get(
+        "bytes_per_launch_at_L", {}) else None
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_sample(L, p, q, seconds, seed=1):
+    """Time the CPU oracle on a band of rows of the same lattice (full width L), enough MCS
+    for about `seconds` of work.  Returns (updates_per_s, cores, description)."""
+    import oracle as o
+    cores = o.threads()
+    nrows = 16
+    gx, gy = o.init_flat_band(L, 0, nrows)
+    t0 = time.perf_counter()
+    o.run_band(L, 0, gx, gy, seed, p, q, t0=0, n_mcs=1)
+    one = time.perf_counter() - t0
+    n = max(1, int(seconds / max(one, 1e-6)))
+    gx, gy = o.init_flat_band(L, 0, nrows)
+    t0 = time.perf_counter()
+    o.run_band(L, 0, gx, gy, seed, p, q, t0=0, n_mcs=n)
+    dt = time.perf_counter() - t0
+    updates = (nrows - 1) * L * n
+    desc = ("oracle (scalar, one site at a time) on a %d-row band of the L=%d lattice, "
+            "p=%g q=%g, %d MCS = %.3g site updates in %.1f s" % (nrows, L, p, q, n, updates, dt))
+    return updates / dt, cores, desc
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    per_step = max(2.0, min(20.0, 60.0 / max(1, a.steps + a.warmup)))
+    for _ in range(a.warmup):
+        oracle_sample(a.L, a.p, a.q, per_step / 4)
+    rates, descs, cores = [], [], 1
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        r, cores, d = oracle_sample(a.L, a.p, a.q, per_step)
+        rates.append(r)
+        descs.append(d)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(rates)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000.0 * wall / max(1, a.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (flat initial surface, seeded Philox)", "impl": "reference",
+            "config": config(a, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": descs[-1]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(a, rank, world, local_rank):
+    import torch
+    import paper_1606_00310_gb300.sca as sca
+    from paper_1606_00310_gb300 import build
+
+    if rank == 0 or not os.path.exists(sca.LIB_PATH):
+        build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.set_device(local_rank)
+    sca.load()
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    times = obs_times(a.mcs)
+    L = a.L
+    updates_per_step = L * L * a.mcs
+    sim = sca.Sim(L, seed=1 + rank, p=a.p, q=a.q, stream=stream, kernel=a.kernel)
+
+    def step():
+        sim.reset()
+        obs = sim.run(times)
+        assert obs[-1].t == a.mcs and all(o.status == 0 for o in obs)
+        return obs
+
+    def sync_all():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(a.warmup):
+        step()
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    gpu_index = vis[local_rank] if len(vis) > local_rank and vis[local_rank].isdigit() else local_rank
+    clocks = ClockSampler(gpu_index)
+    sync_all()
+    launches0 = sca.kernel_launches()
+    sim.timing(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        obs = step()
+    ev1.record(stream)
+    sync_all()
+    launches = sca.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    upd_ms, upd_launches = sim.timing_read()
+    sim.timing(False)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = updates_per_step * a.steps * world / (ms / 1000.0)
+
+    # roofline of the dominant (update) kernel, timed live over the same region
+    fused = (sim.kernel_in_use() == sca.KERNEL_FUSED)
+    kname = "k_fused_mcs" if fused else "k_half_step"
+    upd_per_launch = L * L if fused else L * L // 2
+    alg_bytes = BYTES_PER_UPDATE * upd_per_launch
+    avg_launch_s = upd_ms / 1000.0 / max(1, upd_launches)
+    peak, peak_src = peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": recorded_traffic(kname, L),
+            "kernel": kname, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
+            if peak_src == "measured" else peak_src,
+            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+            "update_share_of_step": upd_ms / ms if ms > 0 else None,
+            "updates_per_s_kernel_only": upd_per_launch / avg_launch_s}
+
+    # end-to-end through the C ABI with host buffers: pinned flat words in, state + W^2 out
+    e2e = None
+    if not a.no_e2e:
+        n_words = sca.words_count(L)
+        host_in = torch.empty(n_words, dtype=torch.int32, pin_memory=True)
+        host_out = torch.empty(n_words, dtype=torch.int32, pin_memory=True)
+        flat = sca.Sim(L, seed=1, p=1.0, q=0.0, stream=stream)   # flat words from the library
+        flat.get_state_ptr(host_in.data_ptr(), n_words)
+        flat.close()
+        del flat
+
+        def e2e_step():
+            sim.set_state_ptr(host_in.data_ptr(), n_words, 0)
+            obs = sim.run(times)
+            sim.get_state_ptr(host_out.data_ptr(), n_words)
+            return obs
+
+        e2e_step()
+        sync_all()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        sync_all()
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        obs_bytes = len(times) * 72
+        e2e = {"value": updates_per_step * a.steps * world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * n_words, "d2h_bytes_per_step": 4 * n_words + obs_bytes,
+               "ms_per_step": 1000.0 * e2e_s / a.steps}
+
+    # context: the paper's own benchmark case p = 1/2, q = 0 (random bits every update)
+    extra = None
+    if not a.no_extra and rank == 0 and (a.p, a.q) == (1.0, 0.0):
+        half = sca.Sim(L, seed=1, p=0.5, q=0.0, stream=stream, kernel=a.kernel)
+        half.step(4)
+        torch.cuda.synchronize(dev)
+        half.timing(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n_half = 64
+        e0.record(stream)
+        half.step(n_half)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        hms = e0.elapsed_time(e1)
+        h_upd_ms, h_launches = half.timing_read()
+        half.close()
+        del half
+        rate = L * L * n_half / (hms / 1000.0)
+        extra = {"workload": "L=65536 p=1/2 q=0 (paper Sec. III headline case), %d MCS" % n_half,
+                 "value": rate, "unit": UNIT,
+                 "paper_titan_black_updates_per_s": 2.29e11,
+                 "ratio_to_paper": rate / 2.29e11,
+                 "hbm_frac": BYTES_PER_UPDATE * L * L * n_half / (h_upd_ms / 1000.0) / 1e9 / peak}
+
+    cpu = None
+    if not a.no_cpu_baseline and rank == 0 and world == 1:
+        r, cores, desc = oracle_sample(L, a.p, a.q, a.cpu_seconds)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic (flat initial surface, seeded Philox)",
+                "config": config(a, world), "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "w2_final": obs[-1].w2}
+        if extra:
+            line["context_p_half"] = extra
+        print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(a, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

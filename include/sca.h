@@ -1,0 +1,174 @@
+/*
+ * sca.h: C ABI of the GB300 octahedron-model stochastic cellular automaton (SCA) library.
+ *
+ * The library advances the 2+1D octahedron (KPZ) surface-growth model of Kelling, Odor and
+ * Gemming, "Bit-Vectorized GPU Implementation of a Stochastic Cellular Automaton Model for
+ * Surface Growth" (arXiv 1606.00310), on one GPU, and measures the surface roughness exactly.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (SCA_OK) on success or a negative SCA_E* status; sca_strerror() names it and
+ *     sca_last_error() gives the detail of the last failure on the calling thread.
+ *   - Pointers named *_dev are device pointers; every other pointer is host memory.
+ *   - Memory passed in by the caller stays owned by the caller and is never freed here.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the library creates and owns a
+ *     non-blocking stream for the object.  Work is enqueued on that stream; calls that return
+ *     host results synchronise it.
+ *   - Types are plain C; no PyTorch or CUDA types appear in the signatures.
+ *
+ * Model (paper Sec. I.A, Eq. 1): slopes sx-, sy- in {-1,+1} per site of an L x L periodic
+ * lattice; a local minimum (sx-, sx+, sy-, sy+) = (-1, +1, -1, +1) turns into the maximum
+ * (+1, -1, +1, -1) with probability p (deposition) and back with probability q (removal).
+ * One Monte-Carlo step (MCS) updates every even site ((x + y) & 1 == 0), then every odd site.
+ *
+ * State format (the only one that crosses this ABI): the "canonical packed words".  A slope
+ * -1 is bit 0, +1 is bit 1 (paper Sec. II.A); sx-(x,y) = h(x,y) - h(x-1,y) and
+ * sy-(x,y) = h(x,y) - h(x,y-1).  With W = L/64 words per sublattice row, the word at index
+ *     ((s * 2 + d) * L + y) * W + j        (s = sublattice, d = 0 for x / 1 for y, row y)
+ * holds in bit b the slope of sublattice site k = 32 j + b, lattice site x = 2k + ((s + y) & 1)
+ * (the paper's role-grouped "non-local" encoding, Sec. II.A, with this offset convention).
+ * Total 4 * L * W words = L*L/4 bytes.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) in place of the paper's TinyMT, keyed by
+ * the seed with counter (g, t, s | (draw - 1) << 1 | (t >> 32) << 6, tag | (g >> 32) << 1):
+ *   - dyadic probabilities (p = P / 2^n, n <= 32; paper Sec. III): draw i = 1..n of packed
+ *     word u = y * W + j uses g = u >> 2, output lane u & 3, tag 0; a site is accepted iff its
+ *     n draw bits, draw 1 most significant, form R >= 2^n - P (equal to the paper's and/or
+ *     construction, xi = r_n; xi = b_i ? r_i | xi : r_i & xi for i = n-1..1);
+ *   - any probability (paper Sec. II.B, one random number per site): site unit
+ *     u = y * (L/2) + k uses g = u >> 2, lane u & 3, draw 1, tag 1; accepted iff the 32-bit
+ *     output < floor(p * 2^32);
+ *   - t is the 0-based index of the MCS being executed; deposition and removal share draws.
+ *
+ * Roughness (paper Sec. I.A names the roughness; its definition here): heights from h(0,0) = 0
+ * down column 0 (sy-) then along each row (sx-); S1 = sum h, S2 = sum h^2 (128-bit),
+ * num = N * S2 - S1^2 (128-bit), W^2 = num / N^2 with N = L*L.
+ */
+#ifndef SCA_H
+#define SCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define SCA_OK 0
+#define SCA_EINVAL (-1)    /* bad argument: L not a positive multiple of 64, p/q outside [0,1],
+                              dyadic mode with a probability that needs more than 32 bits,
+                              decreasing observation times, NULL pointer, short buffer */
+#define SCA_ENOMEM (-2)    /* a library allocation failed */
+#define SCA_ECUDA (-3)     /* a CUDA call or kernel launch failed (detail in sca_last_error) */
+#define SCA_EBUDGET (-4)   /* a request does not fit the server's device-memory budget */
+#define SCA_ETIMEOUT (-5)  /* a wait gave up before the work finished */
+#define SCA_EBUSY (-6)     /* the object is in use (server queue full) */
+#define SCA_ESTATE (-7)    /* the slope state does not close around the torus (heights would
+                              not be single-valued), e.g. after sca_set_state with bad words */
+#define SCA_ENOTFOUND (-8) /* unknown ticket */
+#define SCA_ECANCELED (-9) /* the request was cancelled */
+
+/* ---- random-number modes ------------------------------------------------------------------ */
+#define SCA_RNG_AUTO 0       /* dyadic if p and q are multiples of 2^-32, else per-site */
+#define SCA_RNG_DYADIC 1     /* packed-word draws with the and/or construction (Sec. III)  */
+#define SCA_RNG_UNIFORM32 2  /* one 32-bit uniform per site (Sec. II.B, arbitrary p)       */
+
+typedef struct sca_params {
+    uint32_t L;      /* lateral size: a multiple of 64, 64 <= L <= 131072 */
+    uint32_t rng;    /* SCA_RNG_* */
+    uint64_t seed;   /* Philox key */
+    double p;        /* deposition probability at local minima, 0 <= p <= 1 */
+    double q;        /* removal probability at local maxima, 0 <= q <= 1 */
+} sca_params;
+
+/* One exact roughness observation. */
+typedef struct sca_obs {
+    uint64_t t;        /* MCS completed when observed */
+    uint64_t N;        /* L * L */
+    int64_t S1;        /* sum of heights */
+    uint64_t S2_lo;    /* sum of squared heights, low 64 bits */
+    uint64_t S2_hi;    /*                        high 64 bits */
+    uint64_t num_lo;   /* N * S2 - S1^2, low 64 bits (W^2 = num / N^2) */
+    uint64_t num_hi;   /*                high 64 bits */
+    double w2;         /* num / N^2 rounded to double, for convenience */
+    int32_t status;    /* SCA_OK, or SCA_ESTATE if the slopes did not close */
+    int32_t reserved;
+} sca_obs;
+
+typedef struct sca_sim sca_sim;   /* one simulation: state, stream, scratch; opaque */
+
+/* ---- single lattice ------------------------------------------------------------------------ */
+
+/* Device bytes one simulation of lateral size L needs when the caller supplies the memory
+ * (two state buffers for the ping-pong update, plus observation scratch).  0 if L is invalid. */
+size_t sca_workspace_bytes(uint32_t L);
+
+/* Create a simulation at MCS 0 in the flat state h(x,y) = (x + y) & 1 (sublattice-0 words all
+ * zero, sublattice-1 words all ones).  dev_buf: caller-owned device memory of at least
+ * sca_workspace_bytes(L) bytes, 256-byte aligned, or NULL to let the library allocate.
+ * Errors: SCA_EINVAL (bad params or short buffer), SCA_ENOMEM, SCA_ECUDA. */
+int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_buf_bytes,
+             sca_sim **out);
+
+/* Return to the flat state at MCS 0 (device-side fill, asynchronous on the stream). */
+int sca_reset(sca_sim *sim);
+
+/* Enqueue n_mcs Monte-Carlo steps (Sec. I.A: even sublattice, then odd, per step) on the
+ * simulation's stream.  Asynchronous.  Errors: SCA_EINVAL, SCA_ECUDA. */
+int sca_step(sca_sim *sim, uint64_t n_mcs);
+
+/* Exact roughness of the current state; synchronises the stream.  Errors: SCA_ECUDA; a state
+ * that does not close is reported in out->status = SCA_ESTATE and returned as SCA_ESTATE. */
+int sca_observe(sca_sim *sim, sca_obs *out);
+
+/* Advance to each of the absolute MCS counts times[0..n-1] (non-decreasing, >= the current
+ * count) and observe there; one synchronisation at the end.  out[i] receives observation i.
+ * Errors: SCA_EINVAL, SCA_ECUDA, SCA_ESTATE (first failing observation's status). */
+int sca_run(sca_sim *sim, const uint64_t *times, uint32_t n, sca_obs *out);
+
+/* Copy the current canonical words to host memory (n_words >= 4 * L * L/64); synchronises. */
+int sca_get_state(sca_sim *sim, uint32_t *host_words, size_t n_words);
+
+/* Replace the state by n_words = 4 * L * L/64 canonical words from host memory and set the
+ * MCS count to t (the next step uses MCS index t); synchronises.  The words are not checked
+ * here; sca_observe reports a state that does not close. */
+int sca_set_state(sca_sim *sim, const uint32_t *host_words, size_t n_words, uint64_t t);
+
+/* Device pointer to the current canonical words (valid until the next call on sim). */
+int sca_state_device(sca_sim *sim, uint32_t **words_dev);
+
+/* MCS completed so far. */
+uint64_t sca_time(const sca_sim *sim);
+
+/* Update kernel choice: 0 = automatic, 1 = two-pass (one launch per sublattice, paper
+ * Fig. 3 structure), 2 = fused even+odd wavefront (one launch per MCS).  Results are
+ * identical for every choice; only speed differs.  Errors: SCA_EINVAL. */
+int sca_set_kernel(sca_sim *sim, int kernel);
+
+/* Update kernel the simulation uses now (1 = two-pass, 2 = fused), after automatic choice. */
+int sca_get_kernel(const sca_sim *sim);
+
+/* Kernel timing: while enabled, the library records a CUDA event pair on the simulation's
+ * stream around every run of consecutive update launches (no observation kernels inside).
+ * Enabling clears earlier records.  Errors: SCA_EINVAL, SCA_ECUDA. */
+int sca_timing(sca_sim *sim, int enable);
+
+/* Sum of the recorded update-kernel time in milliseconds and the number of update launches
+ * it covers; synchronises the stream.  Errors: SCA_EINVAL, SCA_ECUDA. */
+int sca_timing_read(sca_sim *sim, double *update_ms, uint64_t *update_launches);
+
+/* Release library-owned memory and stream.  Caller-owned memory is left alone. */
+void sca_free(sca_sim *sim);
+
+/* ---- diagnostics --------------------------------------------------------------------------- */
+const char *sca_strerror(int status);
+const char *sca_last_error(void);   /* detail of the last failure on this thread */
+
+/* Number of kernels this library has launched in this process (all objects, all streams). */
+uint64_t sca_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCA_H */

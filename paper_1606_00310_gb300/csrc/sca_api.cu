@@ -1,0 +1,419 @@
+// C ABI of the single-lattice simulation (declared in include/sca.h).
+//
+// A simulation owns two canonical-word buffers (the fused update reads one and writes the
+// other; the two-pass update works in place), the observation scratch, and a stream.  The
+// host side only validates, lays out memory and enqueues kernels; all dynamics and all
+// observables are computed by the kernels in sca_update.cu / sca_observe.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sca.h"
+#include "sca_internal.h"
+
+static_assert(sizeof(sca_obs) == sizeof(sca::ObsDev), "sca_obs layout");
+
+namespace sca {
+uint64_t launches_total();
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(SCA_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// p = P / 2^n with P odd (n = 0 for p in {0, 1}); false if p is not a multiple of 2^-32.
+static bool split_dyadic(double p, uint32_t &P, uint32_t &n)
+{
+    const double scaled = std::ldexp(p, 32);
+    if (!(scaled >= 0.0 && scaled <= 4294967296.0) || scaled != std::floor(scaled)) return false;
+    uint64_t v = (uint64_t)scaled;
+    if (v == 0) { P = 0; n = 0; return true; }
+    int tz = __builtin_ctzll(v);
+    if (tz > 32) tz = 32;
+    P = (uint32_t)(v >> tz);
+    n = 32u - (uint32_t)tz;
+    return true;
+}
+
+int make_rule(const sca_params &prm, Rule &R)
+{
+    if (!(prm.p >= 0.0 && prm.p <= 1.0) || !(prm.q >= 0.0 && prm.q <= 1.0))
+        return fail(SCA_EINVAL, "p and q must lie in [0, 1]");
+    std::memset(&R, 0, sizeof(R));
+    R.k0 = (uint32_t)prm.seed;
+    R.k1 = (uint32_t)(prm.seed >> 32);
+    uint32_t Pp, np, Pq, nq;
+    const bool dy = split_dyadic(prm.p, Pp, np) && split_dyadic(prm.q, Pq, nq);
+    uint32_t rng = prm.rng;
+    if (rng == SCA_RNG_AUTO) rng = dy ? SCA_RNG_DYADIC : SCA_RNG_UNIFORM32;
+    if (rng == SCA_RNG_DYADIC) {
+        if (!dy) return fail(SCA_EINVAL, "dyadic mode needs p and q to be multiples of 2^-32");
+        R.Pp = Pp; R.np = np; R.Pq = Pq; R.nq = nq;
+        R.n_draws = np > nq ? np : nq;
+        R.mode = R.n_draws == 0 ? 0u : 1u;
+    } else if (rng == SCA_RNG_UNIFORM32) {
+        R.Tp = (uint64_t)std::floor(std::ldexp(prm.p, 32));
+        R.Tq = (uint64_t)std::floor(std::ldexp(prm.q, 32));
+        const bool trivial = (R.Tp == 0 || R.Tp == (1ull << 32)) && (R.Tq == 0 || R.Tq == (1ull << 32));
+        R.mode = trivial ? 0u : 2u;
+        R.Pp = R.Tp == (1ull << 32);   // used when mode == 0
+        R.Pq = R.Tq == (1ull << 32);
+    } else {
+        return fail(SCA_EINVAL, "unknown rng mode");
+    }
+    return SCA_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t state_bytes, off_b, off_h0, off_part, off_res, total;
+};
+constexpr int kResCap = 64;
+
+static bool layout_for(uint32_t L, Layout &lo)
+{
+    if (L < 64 || L % 64 != 0 || L > 131072) return false;
+    const size_t W = L / 64;
+    lo.state_bytes = 4 * (size_t)L * W * sizeof(uint32_t);
+    lo.off_b = align256(lo.state_bytes);
+    lo.off_h0 = lo.off_b + align256(lo.state_bytes);
+    lo.off_part = lo.off_h0 + align256((size_t)L * sizeof(int64_t));
+    lo.off_res = lo.off_part + align256((size_t)(kObsGridCap + 1) * sizeof(ObsPartial));
+    lo.total = lo.off_res + align256((size_t)kResCap * sizeof(ObsDev));
+    return true;
+}
+
+}  // namespace sca
+
+using namespace sca;
+
+struct sca_sim {
+    sca_params P;
+    Rule R;
+    uint32_t L, W;
+    Layout lo;
+    char *base;
+    bool own_mem;
+    uint32_t *buf[2];
+    int cur;
+    int64_t *h0;
+    ObsPartial *part;
+    ObsDev *res;
+    cudaStream_t stream;
+    bool own_stream;
+    uint64_t t;
+    int kernel;
+    bool timing;
+    std::vector<cudaEvent_t> ev;      // start/stop pairs around update launches
+    uint64_t timed_launches;
+};
+
+static void finish_obs(sca_obs &o)
+{
+    const double num = std::ldexp((double)o.num_hi, 64) + (double)o.num_lo;
+    const double N = (double)o.N;
+    o.w2 = num / (N * N);
+}
+
+extern "C" {
+
+size_t sca_workspace_bytes(uint32_t L)
+{
+    Layout lo;
+    return layout_for(L, lo) ? lo.total : 0;
+}
+
+int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_buf_bytes,
+             sca_sim **out)
+{
+    if (!params || !out) return fail(SCA_EINVAL, "NULL argument");
+    *out = nullptr;
+    Layout lo;
+    if (!layout_for(params->L, lo))
+        return fail(SCA_EINVAL, "L must be a multiple of 64 in [64, 131072]");
+    Rule R;
+    int rc = make_rule(*params, R);
+    if (rc) return rc;
+    if (dev_buf) {
+        if (dev_buf_bytes < lo.total) return fail(SCA_EINVAL, "device buffer too small");
+        if ((uintptr_t)dev_buf % 256 != 0) return fail(SCA_EINVAL, "device buffer not 256-byte aligned");
+    }
+    sca_sim *s = new sca_sim();
+    s->P = *params;
+    s->R = R;
+    s->L = params->L;
+    s->W = params->L / 64;
+    s->lo = lo;
+    s->t = 0;
+    s->kernel = 0;
+    s->cur = 0;
+    s->timing = false;
+    s->timed_launches = 0;
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+        s->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete s; return cuda_fail(e, "cudaStreamCreate"); }
+        s->own_stream = true;
+    }
+    if (dev_buf) {
+        s->base = (char *)dev_buf;
+        s->own_mem = false;
+    } else {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, lo.total);
+        if (e != cudaSuccess) {
+            if (s->own_stream) cudaStreamDestroy(s->stream);
+            delete s;
+            return fail(SCA_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        s->base = (char *)p;
+        s->own_mem = true;
+    }
+    s->buf[0] = (uint32_t *)s->base;
+    s->buf[1] = (uint32_t *)(s->base + lo.off_b);
+    s->h0 = (int64_t *)(s->base + lo.off_h0);
+    s->part = (ObsPartial *)(s->base + lo.off_part);
+    s->res = (ObsDev *)(s->base + lo.off_res);
+    int rc2 = sca_reset(s);
+    if (rc2) {
+        sca_free(s);
+        return rc2;
+    }
+    *out = s;
+    return SCA_OK;
+}
+
+int sca_reset(sca_sim *s)
+{
+    if (!s) return fail(SCA_EINVAL, "NULL simulation");
+    // flat surface: sublattice 0 slopes all -1 (bits 0), sublattice 1 all +1 (bits 1)
+    const size_t half = s->lo.state_bytes / 2;
+    cudaError_t e = cudaMemsetAsync(s->buf[s->cur], 0x00, half, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync((char *)s->buf[s->cur] + half, 0xFF, half, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    s->t = 0;
+    return SCA_OK;
+}
+
+int sca_set_kernel(sca_sim *s, int kernel)
+{
+    if (!s || kernel < 0 || kernel > 2) return fail(SCA_EINVAL, "kernel must be 0, 1 or 2");
+    if (kernel == 2 && !fused_supported(s->L))
+        return fail(SCA_EINVAL, "fused kernel needs L to be a multiple of 256");
+    s->kernel = kernel;
+    return SCA_OK;
+}
+
+static bool use_fused(const sca_sim *s)
+{
+    if (s->kernel == 1) return false;
+    if (s->kernel == 2) return true;
+    return fused_supported(s->L);
+}
+
+static cudaError_t record_event(sca_sim *s)
+{
+    cudaEvent_t e;
+    cudaError_t rc = cudaEventCreate(&e);
+    if (rc != cudaSuccess) return rc;
+    s->ev.push_back(e);
+    return cudaEventRecord(e, s->stream);
+}
+
+int sca_get_kernel(const sca_sim *s)
+{
+    if (!s) return fail(SCA_EINVAL, "NULL simulation");
+    return use_fused(s) ? 2 : 1;
+}
+
+static int step_impl(sca_sim *s, uint64_t n)
+{
+    if (n == 0) return SCA_OK;
+    const bool fused = use_fused(s);
+    if (s->timing) {
+        cudaError_t e = record_event(s);
+        if (e != cudaSuccess) return cuda_fail(e, "timing event");
+    }
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t t = s->t + i;
+        cudaError_t e;
+        if (fused) {
+            e = launch_fused_mcs(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, t, s->R, s->stream);
+            if (e == cudaSuccess) s->cur ^= 1;
+        } else {
+            e = launch_half_step(s->buf[s->cur], s->L, t, 0, s->R, s->stream);
+            if (e == cudaSuccess) e = launch_half_step(s->buf[s->cur], s->L, t, 1, s->R, s->stream);
+        }
+        if (e != cudaSuccess) {
+            s->t = t;
+            return cuda_fail(e, "update launch");
+        }
+    }
+    s->t += n;
+    if (s->timing) {
+        s->timed_launches += fused ? n : 2 * n;
+        cudaError_t e = record_event(s);
+        if (e != cudaSuccess) return cuda_fail(e, "timing event");
+    }
+    return SCA_OK;
+}
+
+static void clear_events(sca_sim *s)
+{
+    for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    s->ev.clear();
+    s->timed_launches = 0;
+}
+
+int sca_step(sca_sim *s, uint64_t n_mcs)
+{
+    if (!s) return fail(SCA_EINVAL, "NULL simulation");
+    return step_impl(s, n_mcs);
+}
+
+int sca_run(sca_sim *s, const uint64_t *times, uint32_t n, sca_obs *out)
+{
+    if (!s || (n && (!times || !out))) return fail(SCA_EINVAL, "NULL argument");
+    uint64_t prev = s->t;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (times[i] < prev) return fail(SCA_EINVAL, "observation times must be non-decreasing");
+        prev = times[i];
+    }
+    int first_bad = SCA_OK;
+    uint32_t done = 0;
+    while (done < n) {
+        const uint32_t chunk = (n - done) < (uint32_t)kResCap ? (n - done) : (uint32_t)kResCap;
+        for (uint32_t i = 0; i < chunk; ++i) {
+            int rc = step_impl(s, times[done + i] - s->t);
+            if (rc) return rc;
+            cudaError_t e = launch_observe(s->buf[s->cur], s->L, s->h0, s->part, s->res + i, s->t,
+                                           s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "observe launch");
+        }
+        cudaError_t e = cudaMemcpyAsync(out + done, s->res, chunk * sizeof(ObsDev),
+                                        cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "observe copy");
+        for (uint32_t i = 0; i < chunk; ++i) {
+            finish_obs(out[done + i]);
+            if (out[done + i].status && !first_bad) first_bad = out[done + i].status;
+        }
+        done += chunk;
+    }
+    if (first_bad) return fail(first_bad, "slopes do not close around the torus");
+    return SCA_OK;
+}
+
+int sca_observe(sca_sim *s, sca_obs *out)
+{
+    if (!s || !out) return fail(SCA_EINVAL, "NULL argument");
+    const uint64_t t = s->t;
+    return sca_run(s, &t, 1, out);
+}
+
+int sca_get_state(sca_sim *s, uint32_t *host_words, size_t n_words)
+{
+    if (!s || !host_words) return fail(SCA_EINVAL, "NULL argument");
+    if (n_words * sizeof(uint32_t) < s->lo.state_bytes) return fail(SCA_EINVAL, "host buffer too small");
+    cudaError_t e = cudaMemcpyAsync(host_words, s->buf[s->cur], s->lo.state_bytes,
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? SCA_OK : cuda_fail(e, "sca_get_state");
+}
+
+int sca_set_state(sca_sim *s, const uint32_t *host_words, size_t n_words, uint64_t t)
+{
+    if (!s || !host_words) return fail(SCA_EINVAL, "NULL argument");
+    if (n_words * sizeof(uint32_t) != s->lo.state_bytes) return fail(SCA_EINVAL, "wrong word count");
+    cudaError_t e = cudaMemcpyAsync(s->buf[s->cur], host_words, s->lo.state_bytes,
+                                    cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sca_set_state");
+    s->t = t;
+    return SCA_OK;
+}
+
+int sca_state_device(sca_sim *s, uint32_t **words_dev)
+{
+    if (!s || !words_dev) return fail(SCA_EINVAL, "NULL argument");
+    *words_dev = s->buf[s->cur];
+    return SCA_OK;
+}
+
+uint64_t sca_time(const sca_sim *s) { return s ? s->t : 0; }
+
+int sca_timing(sca_sim *s, int enable)
+{
+    if (!s) return fail(SCA_EINVAL, "NULL simulation");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sca_timing");
+    if (enable) clear_events(s);
+    s->timing = enable != 0;
+    return SCA_OK;
+}
+
+int sca_timing_read(sca_sim *s, double *update_ms, uint64_t *update_launches)
+{
+    if (!s || !update_ms || !update_launches) return fail(SCA_EINVAL, "NULL argument");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sca_timing_read");
+    double total = 0.0;
+    for (size_t i = 0; i + 1 < s->ev.size(); i += 2) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, s->ev[i], s->ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        total += ms;
+    }
+    *update_ms = total;
+    *update_launches = s->timed_launches;
+    return SCA_OK;
+}
+
+void sca_free(sca_sim *s)
+{
+    if (!s) return;
+    clear_events(s);
+    if (s->own_stream) {
+        cudaStreamSynchronize(s->stream);
+        cudaStreamDestroy(s->stream);
+    } else {
+        cudaStreamSynchronize(s->stream);
+    }
+    if (s->own_mem) cudaFree(s->base);
+    delete s;
+}
+
+const char *sca_strerror(int status)
+{
+    switch (status) {
+    case SCA_OK: return "ok";
+    case SCA_EINVAL: return "invalid argument";
+    case SCA_ENOMEM: return "out of device memory";
+    case SCA_ECUDA: return "CUDA error";
+    case SCA_EBUDGET: return "request exceeds the device-memory budget";
+    case SCA_ETIMEOUT: return "timed out";
+    case SCA_EBUSY: return "busy";
+    case SCA_ESTATE: return "slopes do not close around the torus";
+    case SCA_ENOTFOUND: return "unknown ticket";
+    case SCA_ECANCELED: return "cancelled";
+    default: return "unknown status";
+    }
+}
+
+const char *sca_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t sca_kernel_launches(void) { return launches_total(); }
+
+}  // extern "C"

@@ -1,0 +1,213 @@
+// Sublattice update of the octahedron-model SCA on the canonical packed words.
+//
+// Two-pass path (one launch per sublattice, the structure of the paper's algorithm, Fig. 3):
+// a "row team" of threads spans one sublattice row, each thread owning V consecutive words
+// (128 sites for V = 4, read with one 128-bit load per array).  The only couplings between
+// threads are the one-bit shift of sx+ in rows where the neighbour sublattice is offset
+// (Sec. II.B: rows of one parity need the rotated word) and the carry of the mask's top bit
+// into the next word; both go through shared memory with a barrier, as in the paper, but
+// only at team-boundary words (the rest stays in registers).  Rows of one sublattice are
+// independent, so every team works on its own rows in any order.
+#include "sca_internal.h"
+
+namespace sca {
+
+template <int V>
+__device__ __forceinline__ void ld_words(const uint32_t *p, uint32_t (&r)[V])
+{
+    if constexpr (V == 4) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(p);
+        r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
+    } else if constexpr (V == 2) {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        r[0] = q.x; r[1] = q.y;
+    } else {
+        r[0] = *p;
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void st_words(uint32_t *p, const uint32_t (&r)[V])
+{
+    if constexpr (V == 4) {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(r[0], r[1], r[2], r[3]);
+    } else if constexpr (V == 2) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(r[0], r[1]);
+    } else {
+        *p = r[0];
+    }
+}
+
+struct HalfArgs {
+    uint32_t *A;
+    uint32_t L, W;
+    uint64_t t;
+    int s;
+    int T;       // threads owning words in a team
+    int TP;      // padded team size
+    Rule R;
+};
+
+// MODE 0: p, q in {0,1}; 1: dyadic draws; 2: per-site uniform draws.
+template <int V, int MODE>
+__global__ void __launch_bounds__(512) k_half_step(const HalfArgs a)
+{
+    extern __shared__ uint32_t sh[];
+    const int tpb = blockDim.x / a.TP;                  // teams per block
+    const int team = threadIdx.x / a.TP;
+    const int lane = threadIdx.x - team * a.TP;
+    const bool owner = lane < a.T;
+    uint32_t *sh_first = sh + team * a.TP;              // first sx+ source word of each lane
+    uint32_t *sh_carry = sh + tpb * a.TP + team * a.TP; // top mask bit of each lane
+    const int s = a.s, ns = s ^ 1;
+    const uint32_t L = a.L, W = a.W;
+    const size_t plane = (size_t)L * W;
+    uint32_t *Asx = a.A + (size_t)(s * 2 + 0) * plane;
+    uint32_t *Asy = a.A + (size_t)(s * 2 + 1) * plane;
+    uint32_t *Anx = a.A + (size_t)(ns * 2 + 0) * plane;
+    uint32_t *Any = a.A + (size_t)(ns * 2 + 1) * plane;
+
+    for (uint32_t base = blockIdx.x * tpb; base < L; base += gridDim.x * tpb) {
+        const uint32_t y = base + team;
+        const bool active = owner && y < L;
+        const uint32_t j = (uint32_t)lane * V;
+        const size_t row = (size_t)y * W + j;
+        const size_t rown = (size_t)(y + 1 == L ? 0 : y + 1) * W + j;
+        const bool shifted = ((s + y) & 1u) != 0;
+
+        uint32_t xm[V], ym[V], nx[V], ny[V];
+        if (active) {
+            ld_words<V>(Asx + row, xm);
+            ld_words<V>(Asy + row, ym);
+            ld_words<V>(Anx + row, nx);
+            ld_words<V>(Any + rown, ny);
+            sh_first[lane] = nx[0];
+        }
+        __syncthreads();
+        uint32_t m[V];
+        if (active) {
+            uint32_t xpl[V];
+            if (shifted) {
+                const uint32_t next = sh_first[lane + 1 == a.T ? 0 : lane + 1];
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    xpl[v] = (nx[v] >> 1) | ((v + 1 < V ? nx[(v + 1) % V] : next) << 31);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) xpl[v] = nx[v];
+            }
+            uint32_t xip[V], xiq[V];
+            if constexpr (MODE == 0) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    xip[v] = a.R.Pp ? 0xFFFFFFFFu : 0u;
+                    xiq[v] = a.R.Pq ? 0xFFFFFFFFu : 0u;
+                }
+            } else if constexpr (MODE == 1) {
+                xi_dyadic<V>(a.R, row, a.t, s, xip, xiq);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t need = eligible(xm[v], ym[v], xpl[v], ny[v]);
+                    xi_uniform_word(a.R, (uint64_t)y * (L / 2) + 32u * (j + v), a.t, s, need,
+                                    xip[v], xiq[v]);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                m[v] = update_mask(xm[v], ym[v], xpl[v], ny[v], xip[v], xiq[v]);
+                xm[v] ^= m[v];
+                ym[v] ^= m[v];
+                ny[v] ^= m[v];
+            }
+            st_words<V>(Asx + row, xm);
+            st_words<V>(Asy + row, ym);
+            st_words<V>(Any + rown, ny);
+            if (!shifted) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) nx[v] ^= m[v];
+                st_words<V>(Anx + row, nx);
+            } else {
+                sh_carry[lane] = m[V - 1] >> 31;
+            }
+        }
+        __syncthreads();
+        if (active && shifted) {
+            // sx- of the offset neighbour sublattice: site k's partner is site k+1, so the
+            // mask moves up one bit, and word j's top bit enters word j+1 (periodic in x).
+            const uint32_t cin = sh_carry[lane == 0 ? a.T - 1 : lane - 1];
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                nx[v] ^= (m[v] << 1) | (v == 0 ? cin : (m[(v + V - 1) % V] >> 31));
+            st_words<V>(Anx + row, nx);
+        }
+    }
+}
+
+TeamShape team_shape(uint32_t W, int max_block)
+{
+    TeamShape ts;
+    ts.V = (W % 4 == 0) ? 4 : (W % 2 == 0) ? 2 : 1;
+    ts.T = (int)(W / ts.V);
+    if (ts.T <= 32) {
+        int p = 1;
+        while (p < ts.T) p <<= 1;
+        ts.TP = p;
+    } else {
+        ts.TP = (ts.T + 31) / 32 * 32;
+    }
+    ts.teams = ts.TP >= max_block ? 1 : max_block / ts.TP;
+    ts.block = ts.teams * ts.TP;
+    return ts;
+}
+
+static uint64_t g_launches = 0;
+void count_launches(uint64_t n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
+uint64_t launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <int V, int MODE>
+static cudaError_t launch_half_v(const HalfArgs &a, const TeamShape &ts, cudaStream_t st)
+{
+    const int rows_per_block = ts.teams;
+    int grid = (int)((a.L + rows_per_block - 1) / rows_per_block);
+    const int cap = sm_count() * (2048 / ts.block);
+    if (grid > cap) grid = cap;
+    const size_t smem = 2 * sizeof(uint32_t) * ts.block;
+    k_half_step<V, MODE><<<grid, ts.block, smem, st>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_half_step(uint32_t *A, uint32_t L, uint64_t t, int s, const Rule &R,
+                             cudaStream_t st)
+{
+    const uint32_t W = L / 64;
+    const TeamShape ts = team_shape(W, 256);
+    HalfArgs a{A, L, W, t, s, ts.T, ts.TP, R};
+    const int mode = (int)R.mode;
+#define SCA_HALF(VV)                                                        \
+    if (ts.V == VV) {                                                       \
+        if (mode == 0) return launch_half_v<VV, 0>(a, ts, st);              \
+        if (mode == 1) return launch_half_v<VV, 1>(a, ts, st);              \
+        return launch_half_v<VV, 2>(a, ts, st);                             \
+    }
+    SCA_HALF(4)
+    SCA_HALF(2)
+    SCA_HALF(1)
+#undef SCA_HALF
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sca

@@ -1,0 +1,245 @@
+"""Python binding of libsca (include/sca.h): argument marshalling only.
+
+Every step of the dynamics and every observable runs in the library's CUDA kernels.  PyTorch
+supplies device memory (the workspace tensor handed to ``sca_init``) and the stream.  There is
+no fallback: if the compiled library is missing or fails to load, construction raises.
+"""
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsca.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT, EBUSY, ESTATE, ENOTFOUND, ECANCELED = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+RNG_AUTO, RNG_DYADIC, RNG_UNIFORM32 = 0, 1, 2
+KERNEL_AUTO, KERNEL_TWO_PASS, KERNEL_FUSED = 0, 1, 2
+
+
+class sca_params(C.Structure):
+    _fields_ = [("L", C.c_uint32), ("rng", C.c_uint32), ("seed", C.c_uint64),
+                ("p", C.c_double), ("q", C.c_double)]
+
+
+class sca_obs(C.Structure):
+    _fields_ = [("t", C.c_uint64), ("N", C.c_uint64), ("S1", C.c_int64),
+                ("S2_lo", C.c_uint64), ("S2_hi", C.c_uint64),
+                ("num_lo", C.c_uint64), ("num_hi", C.c_uint64),
+                ("w2", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
+# Every symbol include/sca.h declares, with its ctypes signature.
+SIGNATURES = {
+    "sca_workspace_bytes": (C.c_size_t, [C.c_uint32]),
+    "sca_init": (C.c_int, [C.POINTER(sca_params), C.c_void_p, C.c_void_p, C.c_size_t,
+                           C.POINTER(C.c_void_p)]),
+    "sca_reset": (C.c_int, [C.c_void_p]),
+    "sca_step": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "sca_observe": (C.c_int, [C.c_void_p, C.POINTER(sca_obs)]),
+    "sca_run": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.c_uint32, C.POINTER(sca_obs)]),
+    "sca_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "sca_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint64]),
+    "sca_state_device": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sca_time": (C.c_uint64, [C.c_void_p]),
+    "sca_set_kernel": (C.c_int, [C.c_void_p, C.c_int]),
+    "sca_get_kernel": (C.c_int, [C.c_void_p]),
+    "sca_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "sca_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+    "sca_free": (None, [C.c_void_p]),
+    "sca_strerror": (C.c_char_p, [C.c_int]),
+    "sca_last_error": (C.c_char_p, []),
+    "sca_kernel_launches": (C.c_uint64, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsca.so and attach signatures.  Raises if it is missing: no fallback exists."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libsca.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class ScaError(RuntimeError):
+    def __init__(self, code, where):
+        lib = load()
+        msg = "%s: %s (%s)" % (where, lib.sca_strerror(code).decode(),
+                               lib.sca_last_error().decode())
+        super().__init__(msg)
+        self.code = code
+
+
+def check(code, where):
+    if code != OK:
+        raise ScaError(code, where)
+
+
+def workspace_bytes(L: int) -> int:
+    return int(load().sca_workspace_bytes(L))
+
+
+def kernel_launches() -> int:
+    return int(load().sca_kernel_launches())
+
+
+@dataclass
+class Obs:
+    t: int
+    N: int
+    S1: int
+    S2: int
+    num: int
+    w2: float
+    status: int
+
+    @staticmethod
+    def from_c(o: sca_obs) -> "Obs":
+        return Obs(t=int(o.t), N=int(o.N), S1=int(o.S1),
+                   S2=int(o.S2_lo) | (int(o.S2_hi) << 64),
+                   num=int(o.num_lo) | (int(o.num_hi) << 64), w2=float(o.w2),
+                   status=int(o.status))
+
+
+def words_count(L: int) -> int:
+    return 4 * L * (L // 64)
+
+
+class Sim:
+    """One L x L lattice on the current CUDA device, flat at MCS 0.
+
+    ``workspace`` may be a caller-owned uint8 CUDA tensor of at least workspace_bytes(L);
+    otherwise one is allocated with PyTorch.  ``stream`` is a torch.cuda.Stream (default: a new
+    stream of the current device); all of the simulation's kernels run on it."""
+
+    def __init__(self, L, seed=1, p=1.0, q=0.0, rng=RNG_AUTO, stream=None, workspace=None,
+                 kernel=KERNEL_AUTO):
+        import torch
+        lib = load()
+        self.L = int(L)
+        nbytes = workspace_bytes(self.L)
+        if nbytes == 0:
+            raise ScaError(EINVAL, "L=%d" % L)
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        if workspace.numel() * workspace.element_size() < nbytes or not workspace.is_cuda:
+            raise ValueError("workspace must be a CUDA tensor of at least %d bytes" % nbytes)
+        self.workspace = workspace
+        if stream is None:
+            stream = torch.cuda.Stream()
+            stream.wait_stream(torch.cuda.current_stream())   # workspace allocation order
+        self.stream = stream
+        prm = sca_params(L=self.L, rng=rng, seed=seed, p=p, q=q)
+        h = C.c_void_p()
+        check(lib.sca_init(C.byref(prm), C.c_void_p(self.stream.cuda_stream),
+                           C.c_void_p(workspace.data_ptr()), nbytes, C.byref(h)), "sca_init")
+        self._h = h
+        self.params = dict(L=self.L, seed=seed, p=p, q=q, rng=rng)
+        if kernel != KERNEL_AUTO:
+            self.set_kernel(kernel)
+
+    # -- dynamics
+    def reset(self):
+        check(load().sca_reset(self._h), "sca_reset")
+
+    def step(self, n_mcs: int):
+        check(load().sca_step(self._h, int(n_mcs)), "sca_step")
+
+    def set_kernel(self, kernel: int):
+        check(load().sca_set_kernel(self._h, int(kernel)), "sca_set_kernel")
+
+    def kernel_in_use(self) -> int:
+        return int(load().sca_get_kernel(self._h))
+
+    @property
+    def t(self) -> int:
+        return int(load().sca_time(self._h))
+
+    # -- observables
+    def observe(self) -> Obs:
+        o = sca_obs()
+        rc = load().sca_observe(self._h, C.byref(o))
+        if rc not in (OK, ESTATE):
+            check(rc, "sca_observe")
+        return Obs.from_c(o)
+
+    def run(self, times):
+        times = [int(x) for x in times]
+        n = len(times)
+        arr = (C.c_uint64 * n)(*times)
+        out = (sca_obs * n)()
+        rc = load().sca_run(self._h, arr, n, out)
+        if rc not in (OK, ESTATE):
+            check(rc, "sca_run")
+        return [Obs.from_c(o) for o in out]
+
+    # -- kernel timing (CUDA events around update launches on this simulation's stream)
+    def timing(self, enable: bool):
+        check(load().sca_timing(self._h, 1 if enable else 0), "sca_timing")
+
+    def timing_read(self):
+        ms = C.c_double()
+        n = C.c_uint64()
+        check(load().sca_timing_read(self._h, C.byref(ms), C.byref(n)), "sca_timing_read")
+        return float(ms.value), int(n.value)
+
+    # -- state
+    def get_state(self, out: np.ndarray = None) -> np.ndarray:
+        n = words_count(self.L)
+        if out is None:
+            out = np.empty(n, dtype=np.uint32)
+        assert out.dtype == np.uint32 and out.size >= n and out.flags.c_contiguous
+        check(load().sca_get_state(self._h, out.ctypes.data_as(C.c_void_p), n), "sca_get_state")
+        return out
+
+    def set_state(self, words: np.ndarray, t: int = 0):
+        words = np.ascontiguousarray(words, dtype=np.uint32)
+        check(load().sca_set_state(self._h, words.ctypes.data_as(C.c_void_p), words.size, int(t)),
+              "sca_set_state")
+
+    def set_state_ptr(self, host_ptr: int, n_words: int, t: int = 0):
+        """Set the state from a host pointer (e.g. a pinned torch CPU tensor's data_ptr())."""
+        check(load().sca_set_state(self._h, C.c_void_p(host_ptr), int(n_words), int(t)),
+              "sca_set_state")
+
+    def get_state_ptr(self, host_ptr: int, n_words: int):
+        check(load().sca_get_state(self._h, C.c_void_p(host_ptr), int(n_words)), "sca_get_state")
+
+    def state_tensor(self):
+        """The current canonical words as a uint32-viewed slice of the workspace tensor."""
+        import torch
+        p = C.c_void_p()
+        check(load().sca_state_device(self._h, C.byref(p)), "sca_state_device")
+        off = p.value - self.workspace.data_ptr()
+        n = words_count(self.L)
+        torch.cuda.current_stream().wait_stream(self.stream)
+        return self.workspace[off:off + 4 * n].view(torch.int32)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sca_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
