@@ -76,7 +76,7 @@ int make_rule(const sca_params &prm, Rule &R)
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t state_bytes, off_b, off_h0, off_part, off_res, total;
+    size_t state_bytes, off_b, off_h0, off_part, off_res, off_err, total;
 };
 constexpr int kResCap = 64;
 
@@ -89,7 +89,8 @@ static bool layout_for(uint32_t L, Layout &lo)
     lo.off_h0 = lo.off_b + align256(lo.state_bytes);
     lo.off_part = lo.off_h0 + align256((size_t)L * sizeof(int64_t));
     lo.off_res = lo.off_part + align256((size_t)(kObsGridCap + 1) * sizeof(ObsPartial));
-    lo.total = lo.off_res + align256((size_t)kResCap * sizeof(ObsDev));
+    lo.off_err = lo.off_res + align256((size_t)kResCap * sizeof(ObsDev));
+    lo.total = lo.off_err + 256;
     return true;
 }
 
@@ -109,6 +110,7 @@ struct sca_sim {
     int64_t *h0;
     ObsPartial *part;
     ObsDev *res;
+    uint32_t *err;      // device word: bit 0 = a kernel wait gave up
     cudaStream_t stream;
     bool own_stream;
     uint64_t t;
@@ -186,6 +188,14 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
     s->h0 = (int64_t *)(s->base + lo.off_h0);
     s->part = (ObsPartial *)(s->base + lo.off_part);
     s->res = (ObsDev *)(s->base + lo.off_res);
+    s->err = (uint32_t *)(s->base + lo.off_err);
+    {
+        cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(uint32_t), s->stream);
+        if (e != cudaSuccess) {
+            sca_free(s);
+            return cuda_fail(e, "cudaMemsetAsync");
+        }
+    }
     int rc2 = sca_reset(s);
     if (rc2) {
         sca_free(s);
@@ -250,7 +260,8 @@ static int step_impl(sca_sim *s, uint64_t n)
         const uint64_t t = s->t + i;
         cudaError_t e;
         if (fused) {
-            e = launch_fused_mcs(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, t, s->R, s->stream);
+            e = launch_fused_mcs(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, t, s->R, s->err,
+                                 s->stream);
             if (e == cudaSuccess) s->cur ^= 1;
         } else {
             e = launch_half_step(s->buf[s->cur], s->L, t, 0, s->R, s->stream);
@@ -302,10 +313,17 @@ int sca_run(sca_sim *s, const uint64_t *times, uint32_t n, sca_obs *out)
                                            s->stream);
             if (e != cudaSuccess) return cuda_fail(e, "observe launch");
         }
+        uint32_t err = 0;
         cudaError_t e = cudaMemcpyAsync(out + done, s->res, chunk * sizeof(ObsDev),
                                         cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&err, s->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "observe copy");
+        if (err) {
+            cudaMemsetAsync(s->err, 0, sizeof(uint32_t), s->stream);
+            return fail(SCA_ETIMEOUT, "an update kernel's pipeline wait gave up; state invalid");
+        }
         for (uint32_t i = 0; i < chunk; ++i) {
             finish_obs(out[done + i]);
             if (out[done + i].status && !first_bad) first_bad = out[done + i].status;

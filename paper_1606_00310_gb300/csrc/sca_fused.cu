@@ -1,14 +1,371 @@
-// Fused even+odd update (one launch per MCS); filled in below the two-pass path.
+// Fused even+odd update: one launch per MCS, state read once and written once.
+//
+// The paper's kernel (Fig. 3) makes one pass over all rows per sublattice, so every slope bit
+// crosses the memory bus twice in each direction per MCS (Sec. III accounting).  Here one CTA
+// owns a slab of rows [y0, y1) and walks it as a wavefront: the odd half-step of row r-1
+// needs the even half-step of rows r-2, r-1 and r only, so after the even update of row r the
+// odd update of row r-1 can run, and row r-2 is final.  The CTA reads its rows plus a halo of
+// two rows above and two below from the source buffer and writes only its own rows to the
+// destination buffer (ping-pong), so slabs never race.  Halo rows are updated again by the
+// neighbouring slab with identical results because the random bits are a pure function of
+// (seed, MCS, sublattice, word).
+//
+// Data movement: whole lattice rows (all four role planes) stream through a ring of shared
+// memory slots.  One elected thread issues 1D TMA bulk copies (cp.async.bulk) global->shared
+// with an mbarrier per slot and bulk stores shared->global once a row is final; every thread
+// updates its V words per plane in shared memory.  Word-boundary couplings (the rotated sx+
+// word and the mask carry, paper Sec. II.B) go through shared memory: the carry of one
+// half-step is applied after the next barrier, which the pipeline needs anyway.
 #include "sca_internal.h"
 
 namespace sca {
 
-bool fused_supported(uint32_t) { return false; }
-size_t fused_smem_bytes(uint32_t) { return 0; }
-cudaError_t launch_fused_mcs(const uint32_t *, uint32_t *, uint32_t, uint64_t, const Rule &,
-                             cudaStream_t)
+constexpr int kRing = 6;                  // row slots: 3 in use + 3 prefetch/store in flight
+constexpr long long kWaitCycles = 1ll << 31;   // ~1 s at 2 GHz before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    return cudaErrorNotSupported;
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes,
+                                          uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst_smem)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_u32(src_smem)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_wait_read_1()
+{
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+struct FusedArgs {
+    const uint32_t *src;
+    uint32_t *dst;
+    uint32_t L, W;
+    int T;              // threads per CTA = W / V
+    int nslabs;
+    uint64_t t;
+    Rule R;
+    uint32_t *err;      // bit 0: a wait gave up
+};
+
+template <int V>
+__device__ __forceinline__ void lds(const uint32_t *p, uint32_t (&r)[V])
+{
+    if constexpr (V == 4) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(p);
+        r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
+    } else {
+        r[0] = *p;
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void sts(uint32_t *p, const uint32_t (&r)[V])
+{
+    if constexpr (V == 4) {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(r[0], r[1], r[2], r[3]);
+    } else {
+        *p = r[0];
+    }
+}
+
+// One half-step on one row held in shared memory.  own_x/own_y: the updated sublattice's sx-
+// and sy- words of this row; nb_x: the other sublattice's sx- words of this row (sx+ source);
+// nb_yn: the other sublattice's sy- words of the next row (sy+).  In a shifted row the mask
+// enters nb_x one bit up and the top bit of each thread's last word is published in carry[]
+// for the owner of the next word, who applies it after the next barrier.
+template <int V, int MODE>
+__device__ __forceinline__ void half_row(uint32_t *own_x, uint32_t *own_y, uint32_t *nb_x,
+                                         uint32_t *nb_yn, bool shifted, int lane, int T,
+                                         uint32_t W, const Rule &R, uint32_t y, uint32_t L,
+                                         uint64_t t, int s, uint32_t *carry)
+{
+    const uint32_t j = (uint32_t)lane * V;
+    uint32_t xm[V], ym[V], nx[V], ny[V], xpl[V];
+    lds<V>(own_x + j, xm);
+    lds<V>(own_y + j, ym);
+    lds<V>(nb_x + j, nx);
+    lds<V>(nb_yn + j, ny);
+    if (shifted) {
+        const uint32_t next = nb_x[(j + V == W) ? 0 : j + V];   // only bit 0 is used
+#pragma unroll
+        for (int v = 0; v < V; ++v) xpl[v] = (nx[v] >> 1) | ((v + 1 < V ? nx[(v + 1) % V] : next) << 31);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) xpl[v] = nx[v];
+    }
+    uint32_t xip[V], xiq[V];
+    if constexpr (MODE == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            xip[v] = R.Pp ? 0xFFFFFFFFu : 0u;
+            xiq[v] = R.Pq ? 0xFFFFFFFFu : 0u;
+        }
+    } else if constexpr (MODE == 1) {
+        xi_dyadic<V>(R, (uint64_t)y * W + j, t, s, xip, xiq);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t need = eligible(xm[v], ym[v], xpl[v], ny[v]);
+            xi_uniform_word(R, (uint64_t)y * (L / 2) + 32u * (j + v), t, s, need, xip[v], xiq[v]);
+        }
+    }
+    uint32_t m[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        m[v] = update_mask(xm[v], ym[v], xpl[v], ny[v], xip[v], xiq[v]);
+        xm[v] ^= m[v];
+        ym[v] ^= m[v];
+        ny[v] ^= m[v];
+    }
+    sts<V>(own_x + j, xm);
+    sts<V>(own_y + j, ym);
+    sts<V>(nb_yn + j, ny);
+    if (!shifted) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) nx[v] ^= m[v];
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) nx[v] ^= (m[v] << 1) | (v > 0 ? (m[(v + V - 1) % V] >> 31) : 0u);
+        carry[lane] = m[V - 1] >> 31;
+    }
+    sts<V>(nb_x + j, nx);
+    (void)T;
+}
+
+template <int V, int MODE>
+__global__ void __launch_bounds__(512) k_fused_mcs(const FusedArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ volatile int abort_wait;
+    const uint32_t W = a.W, L = a.L;
+    const int T = a.T;
+    const int lane = threadIdx.x;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *cE = reinterpret_cast<uint32_t *>(smem + 64);
+    uint32_t *cO = cE + T;
+    const size_t ring_off = (64 + 8 * (size_t)T + 127) & ~(size_t)127;
+    uint32_t *ring = reinterpret_cast<uint32_t *>(smem + ring_off);
+    const size_t plane = (size_t)L * W;
+    const uint32_t row_bytes = W * 4u;
+
+    const uint32_t b = blockIdx.x;
+    const uint32_t y0 = (uint32_t)(((uint64_t)b * L) / a.nslabs);
+    const uint32_t y1 = (uint32_t)(((uint64_t)(b + 1) * L) / a.nslabs);
+    const int n = (int)(y1 - y0);
+    const int total = n + 4;                 // rows y0-2 .. y1+1
+    auto gy = [&](int r) -> uint32_t { return (uint32_t)(((int64_t)y0 - 2 + r + 2 * (int64_t)L) % L); };
+    auto slot = [&](int r) -> uint32_t * { return ring + (size_t)(r % kRing) * 4 * W; };
+
+    auto issue_load = [&](int r) {
+        uint64_t *bar = &full[r % kRing];
+        mbar_expect_tx(bar, 4 * row_bytes);
+        uint32_t *d = slot(r);
+        const size_t row = (size_t)gy(r) * W;
+#pragma unroll
+        for (int pl = 0; pl < 4; ++pl)
+            bulk_load(d + (size_t)pl * W, a.src + (size_t)pl * plane + row, row_bytes, bar);
+    };
+    auto wait_row = [&](int r) {
+        uint64_t *bar = &full[r % kRing];
+        const uint32_t parity = (uint32_t)((r / kRing) & 1);
+        if (mbar_try_wait(bar, parity)) return;
+        const long long start = clock64();
+        while (!abort_wait) {
+            if (mbar_try_wait(bar, parity)) return;
+            if (clock64() - start > kWaitCycles) {
+                abort_wait = 1;
+                atomicOr(a.err, 1u);
+            }
+        }
+    };
+    auto store_row = [&](int r) {
+        const uint32_t *sl = slot(r);
+        const size_t row = (size_t)gy(r) * W;
+#pragma unroll
+        for (int pl = 0; pl < 4; ++pl) bulk_store(a.dst + (size_t)pl * plane + row, sl + (size_t)pl * W, row_bytes);
+        bulk_commit();
+    };
+    // plane order in a slot: 0 = A[0][x], 1 = A[0][y], 2 = A[1][x], 3 = A[1][y]
+    auto even_row = [&](int r) {      // sublattice 0 at row r, reads rows r and r+1
+        const uint32_t y = gy(r);
+        uint32_t *cur = slot(r), *nxt = slot(r + 1);
+        half_row<V, MODE>(cur, cur + W, cur + 2 * W, nxt + 3 * W, (y & 1u) != 0, lane, T, W, a.R,
+                          y, L, a.t, 0, cE);
+    };
+    auto odd_row = [&](int r) {       // sublattice 1 at row r, reads rows r and r+1
+        const uint32_t y = gy(r);
+        uint32_t *cur = slot(r), *nxt = slot(r + 1);
+        half_row<V, MODE>(cur + 2 * W, cur + 3 * W, cur, nxt + W, (y & 1u) == 0, lane, T, W, a.R,
+                          y, L, a.t, 1, cO);
+    };
+    auto prev_lane = [&]() { return lane == 0 ? T - 1 : lane - 1; };
+
+    if (lane == 0) {
+        abort_wait = 0;
+        for (int i = 0; i < kRing; ++i) mbar_init(&full[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (lane == 0)
+        for (int r = 0; r < kRing && r < total; ++r) issue_load(r);
+
+    wait_row(0);
+    wait_row(1);
+    even_row(0);          // only its sy+ effect on row 1 matters
+    for (int r = 1; r <= n + 2; ++r) {
+        wait_row(r + 1);
+        // phase E: finish the odd update of row r-2 (its carry), then the even update of row r
+        if (r - 2 >= 1 && (gy(r - 2) & 1u) == 0)
+            slot(r - 2)[(size_t)lane * V] ^= cO[prev_lane()];
+        even_row(r);
+        fence_proxy_async();
+        __syncthreads();
+        // phase O: finish the even update of row r, odd update of row r-1, emit row r-2
+        if (gy(r) & 1u) slot(r)[2 * W + (size_t)lane * V] ^= cE[prev_lane()];
+        if (r >= 2) odd_row(r - 1);
+        if (lane == 0) {
+            if (r - 2 >= 2) store_row(r - 2);
+            const int refill = r + 3;       // into the slot of row r-3, stored one step ago
+            if (r - 3 >= 0 && refill < total && refill >= kRing) {
+                bulk_wait_read_1();
+                issue_load(refill);
+            }
+        }
+        __syncthreads();
+    }
+    // epilogue: carry of the odd update of row n+1 (= y1-1), then emit it
+    if ((gy(n + 1) & 1u) == 0) slot(n + 1)[(size_t)lane * V] ^= cO[prev_lane()];
+    fence_proxy_async();
+    __syncthreads();
+    if (lane == 0) {
+        store_row(n + 1);
+        bulk_wait_all();
+        if (abort_wait) {
+            // a wait gave up: let the loads still in flight land before shared memory goes
+            // away (each slot's last load, bounded like every other wait)
+            for (int k = 0; k < kRing && k < total; ++k) {
+                const int last = k + ((total - 1 - k) / kRing) * kRing;
+                const long long start = clock64();
+                while (!mbar_try_wait(&full[k], (uint32_t)((last / kRing) & 1)) &&
+                       clock64() - start < kWaitCycles) {
+                }
+            }
+        }
+    }
+}
+
+static int fused_V(uint32_t W) { return (W % 128 == 0) ? 4 : 1; }
+
+bool fused_supported(uint32_t L)
+{
+    if (L % 2048 != 0) return false;
+    const uint32_t W = L / 64;
+    const int V = fused_V(W);
+    const int T = (int)(W / V);
+    return T >= 32 && T <= 512 && T % 32 == 0;
+}
+
+size_t fused_smem_bytes(uint32_t L)
+{
+    const uint32_t W = L / 64;
+    const int T = (int)(W / fused_V(W));
+    const size_t ring_off = (64 + 8 * (size_t)T + 127) & ~(size_t)127;
+    return ring_off + (size_t)kRing * 4 * W * sizeof(uint32_t);
+}
+
+template <int V, int MODE>
+static cudaError_t launch_fused_v(FusedArgs a, size_t smem, cudaStream_t st)
+{
+    auto kern = k_fused_mcs<V, MODE>;
+    static int configured_smem = 0;
+    if ((int)smem > configured_smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured_smem = (int)smem;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, a.T, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = sm_count() * per_sm;
+    const int max_slabs = (int)(a.L / 8);     // at least 8 rows per slab
+    if (grid > max_slabs) grid = max_slabs;
+    a.nslabs = grid;
+    kern<<<grid, a.T, smem, st>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_mcs(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t,
+                             const Rule &R, uint32_t *err, cudaStream_t st)
+{
+    if (!fused_supported(L)) return cudaErrorNotSupported;
+    const uint32_t W = L / 64;
+    const int V = fused_V(W);
+    FusedArgs a{src, dst, L, W, (int)(W / V), 0, t, R, err};
+    const size_t smem = fused_smem_bytes(L);
+    const int mode = (int)R.mode;
+    if (V == 4) {
+        if (mode == 0) return launch_fused_v<4, 0>(a, smem, st);
+        if (mode == 1) return launch_fused_v<4, 1>(a, smem, st);
+        return launch_fused_v<4, 2>(a, smem, st);
+    }
+    if (mode == 0) return launch_fused_v<1, 0>(a, smem, st);
+    if (mode == 1) return launch_fused_v<1, 1>(a, smem, st);
+    return launch_fused_v<1, 2>(a, smem, st);
 }
 
 }  // namespace sca

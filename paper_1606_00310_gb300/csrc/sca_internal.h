@@ -38,8 +38,9 @@ struct ObsPartial {
 // for the fused path.  Launch counts are added to the library's counter.
 cudaError_t launch_half_step(uint32_t *A, uint32_t L, uint64_t t, int s, const Rule &R,
                              cudaStream_t st);
+// err: device word; bit 0 is set if a pipeline wait gave up (the result is then invalid).
 cudaError_t launch_fused_mcs(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t,
-                             const Rule &R, cudaStream_t st);
+                             const Rule &R, uint32_t *err, cudaStream_t st);
 bool fused_supported(uint32_t L);
 size_t fused_smem_bytes(uint32_t L);
 

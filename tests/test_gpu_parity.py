@@ -232,3 +232,35 @@ def test_large_lattice_p1_closed_form(sca):
         obs = sim.run([1, 2, 4, 8])
         assert torch.equal(sim.state_tensor(), flat)
     assert all(4 * g.num == g.N ** 2 for g in obs)
+
+
+FUSED_CASES = [
+    (2048, 0.5, 0.0, 1), (2048, 0.7, 0.3, 2), (6144, 0.75, 0.25, 1),
+    (8192, 0.875, 0.125, 1), (16384, 0.5, 0.5, 1), (8192, 0.95, 0.0, 2), (8192, 1.0, 0.0, 1),
+]
+
+
+@pytest.mark.parametrize("L,p,q,mode", FUSED_CASES)
+def test_fused_equals_two_pass(sca, L, p, q, mode):
+    """The fused one-launch-per-MCS kernel and the two-pass kernel give identical states and
+    sums (the choice of kernel changes speed only)."""
+    times = [1, 2, 5, 9]
+    res = []
+    for kernel in (sca.KERNEL_TWO_PASS, sca.KERNEL_FUSED):
+        with sca.Sim(L, seed=31, p=p, q=q, rng=mode, kernel=kernel) as sim:
+            assert sim.kernel_in_use() == kernel
+            obs = sim.run(times)
+            res.append(([(o.S1, o.S2, o.num) for o in obs], sim.get_state()))
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1])
+
+
+def test_fused_against_oracle(sca):
+    L, seed, p, q = 2048, 3, 0.625, 0.125
+    times = [1, 2, 3, 6]
+    with sca.Sim(L, seed=seed, p=p, q=q, kernel=sca.KERNEL_FUSED) as sim:
+        obs = sim.run(times)
+        words = sim.get_state()
+    words_o, ora = oracle_run_obs(L, seed, p, q, times)
+    assert_obs_equal(obs, ora)
+    assert np.array_equal(words, words_o)
