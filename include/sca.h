@@ -160,6 +160,26 @@ int sca_timing_read(sca_sim *sim, double *update_ms, uint64_t *update_launches);
 /* Release library-owned memory and stream.  Caller-owned memory is left alone. */
 void sca_free(sca_sim *sim);
 
+/* ---- observation without allocation ---------------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot let the
+ * library allocate device memory (a host application that owns all GPU memory through its own
+ * pool, a plug-in barred from the CUDA allocator, a loop that must not pay for cudaMalloc or
+ * its implicit device synchronisation).  It computes the same exact roughness as sca_observe
+ * for canonical words the caller already holds, using a fixed file-scope device array of
+ * 590,336 bytes as scratch (held by every GPU that loads this library until the process exits).
+ *   words_dev: caller-owned device memory with 4 * L * L/64 canonical words (read only).
+ *   L:         multiple of 64, 64 <= L <= 65536; larger L is rejected with SCA_EINVAL because
+ *              the column-0 heights would not fit the scratch array.
+ *   t:         copied into out->t.
+ *   stream:    cudaStream_t as void*, NULL for the legacy default stream; synchronised.
+ *   out:       host result, as from sca_observe (SCA_ESTATE if the slopes do not close).
+ * The first call on each device looks up the array's device address with that device current;
+ * make that first call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller.  Each call overwrites all the
+ * scratch it reads, so nothing carries over between calls.  No allocation or free is made. */
+int sca_observe_noalloc(const uint32_t *words_dev, uint32_t L, uint64_t t, void *stream,
+                        sca_obs *out);
+
 /* ---- diagnostics --------------------------------------------------------------------------- */
 const char *sca_strerror(int status);
 const char *sca_last_error(void);   /* detail of the last failure on this thread */

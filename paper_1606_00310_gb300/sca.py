@@ -49,6 +49,8 @@ SIGNATURES = {
     "sca_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     "sca_free": (None, [C.c_void_p]),
+    "sca_observe_noalloc": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint64, C.c_void_p,
+                                      C.POINTER(sca_obs)]),
     "sca_strerror": (C.c_char_p, [C.c_int]),
     "sca_last_error": (C.c_char_p, []),
     "sca_kernel_launches": (C.c_uint64, []),
@@ -111,6 +113,17 @@ class Obs:
                    S2=int(o.S2_lo) | (int(o.S2_hi) << 64),
                    num=int(o.num_lo) | (int(o.num_hi) << 64), w2=float(o.w2),
                    status=int(o.status))
+
+
+def observe_noalloc(words_dev_ptr: int, L: int, t: int = 0, stream=None) -> Obs:
+    """Exact roughness of caller-owned device words without any library allocation (the
+    scratch is a fixed device array shared by all calls; serialise overlapping calls)."""
+    o = sca_obs()
+    st = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    rc = load().sca_observe_noalloc(C.c_void_p(words_dev_ptr), int(L), int(t), st, C.byref(o))
+    if rc not in (OK, ESTATE):
+        check(rc, "sca_observe_noalloc")
+    return Obs.from_c(o)
 
 
 def words_count(L: int) -> int:
