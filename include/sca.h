@@ -160,6 +160,50 @@ int sca_timing_read(sca_sim *sim, double *update_ms, uint64_t *update_launches);
 /* Release library-owned memory and stream.  Caller-owned memory is left alone. */
 void sca_free(sca_sim *sim);
 
+/* ---- batched ensemble ------------------------------------------------------------------------
+ * Many independent lattices (each its own L, seed, p, q, rng mode) advanced together by one
+ * persistent kernel launch, captured in a CUDA graph and replayed while the observation times
+ * repeat.  Each lattice stays in on-chip shared memory for the whole run; lattices too large
+ * for one CTA are split by rows over up to 8 CTAs of a thread-block cluster that exchange the
+ * boundary sy+ row through distributed shared memory.  Every lattice follows exactly the
+ * single-lattice dynamics (same canonical words, same Philox counters), so its result equals
+ * a sca_sim run with the same parameters, alone or in any mix. */
+typedef struct sca_batch sca_batch;   /* opaque */
+
+/* Create `count` lattices, all flat at MCS 0.  params[i].L must be a multiple of 64 in
+ * [128, 2048].  The library allocates the states (sum of L*L/4 bytes) and result buffers.
+ * Errors: SCA_EINVAL, SCA_ENOMEM, SCA_ECUDA. */
+int sca_batch_init(const sca_params *params, uint32_t count, void *stream, sca_batch **out);
+
+/* Launch shape: cluster size (1, 2, 4, 8 or 16 CTAs) and threads per CTA (128..512).  Every
+ * shape gives identical results; sca_batch_tune picks the fastest.  Errors: SCA_EINVAL when a
+ * lattice does not fit the cluster's shared memory. */
+int sca_batch_set_shape(sca_batch *b, int cluster, int threads);
+int sca_batch_get_shape(const sca_batch *b, int *cluster, int *threads, int *clusters_launched,
+                        int *units);
+
+/* Autotuner: times a probe_mcs-MCS run for each launch shape that fits (cluster sizes 4, 8, 16;
+ * 256, 384, 512 threads), keeps the fastest, and leaves every lattice flat at MCS 0.  The
+ * chosen shape is returned through best_cluster / best_threads (either may be NULL).  Only
+ * speed depends on the shape.  Errors: SCA_EINVAL, SCA_ECUDA. */
+int sca_batch_tune(sca_batch *b, uint32_t probe_mcs, int *best_cluster, int *best_threads);
+
+/* Advance every lattice to each time in times[0..n-1] (increasing, after the current MCS,
+ * n <= 64) in one graph launch and observe there.  out (may be NULL) receives count * n records,
+ * lattice-major (out[i * n + k] = lattice i at times[k]); ensemble_w2 (may be NULL) receives n
+ * ensemble means of W^2, summed in lattice order.  Synchronises.  Errors: SCA_EINVAL, SCA_ECUDA,
+ * SCA_ESTATE. */
+int sca_batch_run(sca_batch *b, const uint64_t *times, uint32_t n, sca_obs *out,
+                  double *ensemble_w2);
+
+/* Canonical words of lattice `index` (4 * L * L/64 words) to host memory; synchronises. */
+int sca_batch_get_state(sca_batch *b, uint32_t index, uint32_t *host_words, size_t n_words);
+
+/* All lattices back to flat at MCS 0 (asynchronous). */
+int sca_batch_reset(sca_batch *b);
+uint64_t sca_batch_time(const sca_batch *b);
+void sca_batch_free(sca_batch *b);
+
 /* ---- observation without allocation ---------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot let the
  * library allocate device memory (a host application that owns all GPU memory through its own

@@ -1,0 +1,848 @@
+// Batched ensemble: many independent lattices of uneven size in one persistent launch.
+//
+// Each lattice lives in shared memory for its whole run, so the dynamics never touch HBM
+// after the first load (the paper's update, Sec. II.B Eqs. 2-4, applied to words held on
+// chip).  A lattice too large for one CTA is split by rows over G CTAs of a thread-block
+// cluster; the only coupling between parts is the sy+ plane row just below a part (Sec. II.A:
+// sy+(x,y) = sy-(x,y+1)), which the part above reads and updates directly in its neighbour's
+// shared memory (DSMEM).  Work units (the lattices of one cluster: one lattice over 8 CTAs,
+// or a few smaller ones) are pulled from a device counter by whole clusters; all CTAs of a
+// cluster run the same MCS count, so one cluster barrier after each half-step (Sec. I.A: all
+// even sites, then all odd sites) keeps the parts of a lattice consistent.  Roughness is
+// computed in shared memory at the requested times and written as exact per-part partials.
+#include <cooperative_groups.h>
+#include <cstring>
+#include <mutex>
+
+#include "sca_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace sca {
+
+struct BatchLattice {
+    uint64_t state_off;  // word offset of its canonical words in the batch buffer
+    uint32_t L, W, G, V; // size, words per sublattice row, CTAs sharing it, words per item
+    uint32_t part_off;   // first partial: part_off + obs * G + part
+    uint32_t pad;
+    Rule R;
+};
+
+struct BatchSlot {
+    int32_t lattice;     // -1: this CTA idles in the unit
+    int32_t part;
+};
+
+struct BatchArgs {
+    uint32_t *state;
+    const BatchLattice *lat;
+    const BatchSlot *slots;    // n_units x C
+    int n_units, C;
+    uint32_t *unit_counter;
+    const uint64_t *times;
+    int n_times;
+    uint64_t t0;
+    ObsPartial *partials;
+};
+
+// One item of a half-step in shared memory: V words of one row.  In a shifted row the mask
+// enters the neighbour sublattice's sx- one bit up; the first word of every item is updated
+// with a shared-memory atomic xor because the item to its left xors its carry bit into it.
+template <int V, int MODE>
+__device__ __forceinline__ void batch_item(uint32_t *own_x, uint32_t *own_y, uint32_t *nb_x,
+                                           uint32_t *nb_yn, uint32_t j, uint32_t W, bool shifted,
+                                           const Rule &R, uint32_t y, uint32_t L, uint64_t t, int s)
+{
+    uint32_t xm[V], ym[V], nx[V], ny[V], xpl[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        xm[v] = own_x[j + v];
+        ym[v] = own_y[j + v];
+        nx[v] = nb_x[j + v];
+        ny[v] = nb_yn[j + v];
+    }
+    if (shifted) {
+        const uint32_t jn = (j + V == W) ? 0u : j + V;
+        const uint32_t next = nb_x[jn];   // bit 0 only; nobody changes it before our own xor
+#pragma unroll
+        for (int v = 0; v < V; ++v) xpl[v] = (nx[v] >> 1) | ((v + 1 < V ? nx[(v + 1) % V] : next) << 31);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) xpl[v] = nx[v];
+    }
+    uint32_t xip[V], xiq[V];
+    if constexpr (MODE == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            xip[v] = R.Pp ? 0xFFFFFFFFu : 0u;
+            xiq[v] = R.Pq ? 0xFFFFFFFFu : 0u;
+        }
+    } else if constexpr (MODE == 1) {
+        xi_dyadic<V>(R, (uint64_t)y * W + j, t, s, xip, xiq);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t need = eligible(xm[v], ym[v], xpl[v], ny[v]);
+            xi_uniform_word(R, (uint64_t)y * (L / 2) + 32u * (j + v), t, s, need, xip[v], xiq[v]);
+        }
+    }
+    uint32_t m[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        m[v] = update_mask(xm[v], ym[v], xpl[v], ny[v], xip[v], xiq[v]);
+        own_x[j + v] = xm[v] ^ m[v];
+        own_y[j + v] = ym[v] ^ m[v];
+        nb_yn[j + v] = ny[v] ^ m[v];
+    }
+    if (!shifted) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) nb_x[j + v] = nx[v] ^ m[v];
+    } else {
+        atomicXor(&nb_x[j], m[0] << 1);
+#pragma unroll
+        for (int v = 1; v < V; ++v) nb_x[j + v] = nx[v] ^ ((m[v] << 1) | (m[v - 1] >> 31));
+        atomicXor(&nb_x[(j + V == W) ? 0u : j + V], m[V - 1] >> 31);
+    }
+}
+
+template <int V, int MODE>
+__device__ void batch_half_step(uint32_t *sm, const BatchLattice &lt, uint32_t R, uint32_t r0,
+                                uint32_t *remote_nb_y, int s, uint64_t t)
+{
+    const uint32_t W = lt.W;
+    const size_t P = (size_t)R * W;
+    uint32_t *own_x = sm + (size_t)(s * 2 + 0) * P;
+    uint32_t *own_y = sm + (size_t)(s * 2 + 1) * P;
+    uint32_t *nbx = sm + (size_t)((s ^ 1) * 2 + 0) * P;
+    uint32_t *nby = sm + (size_t)((s ^ 1) * 2 + 1) * P;
+    const uint32_t per_row = W / V;
+    const uint32_t items = R * per_row;
+    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+        const uint32_t r = it / per_row;
+        const uint32_t j = (it - r * per_row) * V;
+        const uint32_t y = r0 + r;
+        uint32_t *nyn = (r + 1 < R) ? nby + (size_t)(r + 1) * W : remote_nb_y;
+        batch_item<V, MODE>(own_x + (size_t)r * W, own_y + (size_t)r * W, nbx + (size_t)r * W, nyn,
+                            j, W, ((uint32_t)s + y) & 1u, lt.R, y, lt.L, t, s);
+    }
+}
+
+template <int V>
+__device__ void batch_half_step_v(uint32_t *sm, const BatchLattice &lt, uint32_t R, uint32_t r0,
+                                  uint32_t *remote_nb_y, int s, uint64_t t)
+{
+    if (lt.R.mode == 0) batch_half_step<V, 0>(sm, lt, R, r0, remote_nb_y, s, t);
+    else if (lt.R.mode == 1) batch_half_step<V, 1>(sm, lt, R, r0, remote_nb_y, s, t);
+    else batch_half_step<V, 2>(sm, lt, R, r0, remote_nb_y, s, t);
+}
+
+__device__ __forceinline__ int64_t warp_scan_incl(int64_t v, int width)
+{
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < width; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xFFFFFFFFu, v, o, width);
+        if ((lane & (width - 1)) >= o) v += u;
+    }
+    return v;
+}
+
+// Exclusive prefix over the block of one value per thread (thread order); also the total.
+__device__ int64_t block_excl_scan(int64_t v, int64_t *ws, int64_t &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t incl = warp_scan_incl(v, 32);
+    __syncthreads();
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t x = lane < nw ? ws[lane] : 0;
+        x = warp_scan_incl(x, 32);
+        ws[lane] = x;
+    }
+    __syncthreads();
+    total = ws[nw - 1];
+    return incl - v + (wid > 0 ? ws[wid - 1] : 0);
+}
+
+struct ObsShared {
+    int64_t ws[32];
+    int64_t red1[32];
+    unsigned long long red2[32];
+    uint32_t flag;
+    int64_t colsum;          // this part's sum of sy-(0,y) over its rows with y >= 1
+    int64_t colsum_all;      // including y = 0
+};
+
+// Roughness partial of this CTA's rows at one observation (all CTAs of the cluster call it).
+__device__ void batch_observe(cg::cluster_group &cluster, uint32_t *sm, int32_t *h0, bool have,
+                              const BatchLattice &lt, int part, uint32_t R, int base_rank,
+                              ObsShared &os, ObsPartial *out)
+{
+    const uint32_t W = have ? lt.W : 1;
+    const size_t P = (size_t)R * W;
+    const uint32_t r0 = (uint32_t)part * R;
+    // column 0: site (0,y) is site 0 of sublattice y & 1; its sy- is bit 0 of word 0
+    auto s0y = [&](uint32_t r) -> int64_t {
+        const uint32_t y = r0 + r;
+        return 2 * (int64_t)(sm[(size_t)((y & 1u) * 2 + 1) * P + (size_t)r * W] & 1u) - 1;
+    };
+    const uint32_t per = have ? (R + blockDim.x - 1) / blockDim.x : 0;
+    const uint32_t ra = threadIdx.x * per;
+    int64_t loc = 0, loc_all = 0;
+    for (uint32_t r = ra; r < ra + per && r < R; ++r) {
+        const int64_t v = s0y(r);
+        loc_all += v;
+        if (r0 + r > 0) loc += v;
+    }
+    if (threadIdx.x == 0) os.flag = 0;
+    int64_t tot_all;
+    block_excl_scan(loc_all, os.ws, tot_all);
+    int64_t tot;
+    const int64_t excl = block_excl_scan(loc, os.ws, tot);
+    if (threadIdx.x == 0) {
+        os.colsum = tot;
+        os.colsum_all = tot_all;
+    }
+    cluster.sync();
+    int64_t offset = 0;
+    if (have) {
+        for (int q = 0; q < part; ++q)
+            offset += cluster.map_shared_rank(&os, base_rank + q)->colsum;
+        if (part == 0 && threadIdx.x == 0) {
+            int64_t all = 0;
+            for (uint32_t q = 0; q < lt.G; ++q) all += cluster.map_shared_rank(&os, base_rank + q)->colsum_all;
+            if (all != 0) os.flag |= 1u;      // column 0 does not close around y
+        }
+        int64_t run = offset + excl;
+        for (uint32_t r = ra; r < ra + per && r < R; ++r) {
+            if (r0 + r > 0) run += s0y(r);
+            h0[r] = (int32_t)run;
+        }
+    }
+    __syncthreads();
+    int64_t s1 = 0;
+    unsigned long long s2 = 0;
+    uint32_t flags = 0;
+    if (have) {
+        int TP = 1;
+        while (TP < (int)W) TP <<= 1;
+        const int teams = blockDim.x / TP;
+        const int team = threadIdx.x / TP, lane = threadIdx.x - team * TP;
+        const int wl = threadIdx.x & 31;
+        const uint32_t rounds = (R + teams - 1) / teams;
+        for (uint32_t k = 0; k < rounds; ++k) {
+            const uint32_t r = k * teams + team;
+            const bool act = r < R && lane < (int)W && team < teams;
+            uint32_t e = 0, o = 0;
+            int64_t c = 0;
+            const uint32_t y = r0 + r;
+            if (act) {
+                e = sm[(size_t)((y & 1u) * 2) * P + (size_t)r * W + lane];
+                o = sm[(size_t)(((y & 1u) ^ 1u) * 2) * P + (size_t)r * W + lane];
+                c = 2 * (__popc(e) + __popc(o)) - 64;
+            }
+            const int64_t incl = warp_scan_incl(c, TP);
+            const int64_t total = __shfl_sync(0xFFFFFFFFu, incl, (wl & ~(TP - 1)) + TP - 1);
+            if (act) {
+                if (lane == 0 && total != 0) flags |= 2u;   // row does not close around x
+                const int64_t s0 = 2 * (int64_t)(sm[(size_t)((y & 1u) * 2) * P + (size_t)r * W] & 1u) - 1;
+                const int64_t H = (int64_t)h0[r] + incl - c - s0;
+                int32_t d = 0, sd = 0, sd2 = 0;
+#pragma unroll 8
+                for (int b = 0; b < 32; ++b) {
+                    d += 2 * (int32_t)((e >> b) & 1u) - 1;
+                    sd += d;
+                    sd2 += d * d;
+                    d += 2 * (int32_t)((o >> b) & 1u) - 1;
+                    sd += d;
+                    sd2 += d * d;
+                }
+                s1 += 64 * H + sd;
+                s2 += (unsigned long long)(64 * H * H + 2 * H * (int64_t)sd + (int64_t)sd2);
+            }
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_down_sync(0xFFFFFFFFu, s1, off);
+        s2 += __shfl_down_sync(0xFFFFFFFFu, s2, off);
+    }
+    if (flags) atomicOr(&os.flag, flags);
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        os.red1[wid] = s1;
+        os.red2[wid] = s2;
+    }
+    __syncthreads();
+    if (have && threadIdx.x == 0) {
+        int64_t t1 = 0;
+        unsigned long long t2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t1 += os.red1[w];
+            t2 += os.red2[w];
+        }
+        out->s1 = t1;
+        out->s2_lo = t2;
+        out->s2_hi = 0;
+        out->flags = os.flag;
+    }
+    cluster.sync();   // neighbours are done reading colsum before it is reused
+}
+
+__global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ int s_unit;
+    __shared__ ObsShared os;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const uint64_t t_end = a.times[a.n_times - 1];
+
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) s_unit = (int)atomicAdd(a.unit_counter, 1u);
+        cluster.sync();
+        const int unit = *cluster.map_shared_rank(&s_unit, 0);
+        cluster.sync();
+        if (unit >= a.n_units) break;
+        const BatchSlot slot = a.slots[(size_t)unit * a.C + rank];
+        const bool have = slot.lattice >= 0;
+        BatchLattice lt;
+        if (have) lt = a.lat[slot.lattice];
+        else { lt.L = 64; lt.W = 1; lt.G = 1; lt.V = 1; }
+        const uint32_t R = have ? lt.L / lt.G : 0;
+        const uint32_t W = lt.W;
+        const uint32_t r0 = have ? (uint32_t)slot.part * R : 0;
+        const int base_rank = rank - (have ? slot.part : 0);
+        const size_t P = (size_t)R * W;
+        int32_t *h0 = reinterpret_cast<int32_t *>(sm + 4 * P);
+        // the sy- plane of the other sublattice, first row of the next part (periodic)
+        uint32_t *remote_y[2] = {nullptr, nullptr};
+        if (have) {
+            const int nrank = base_rank + (int)((slot.part + 1) % lt.G);
+            remote_y[0] = cluster.map_shared_rank(sm + (size_t)(1 * 2 + 1) * P, nrank);
+            remote_y[1] = cluster.map_shared_rank(sm + (size_t)(0 * 2 + 1) * P, nrank);
+            const uint32_t *g = a.state + lt.state_off;
+            const size_t plane = (size_t)lt.L * W;
+            for (uint32_t i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+                const uint32_t pl = (uint32_t)(i / P), k = (uint32_t)(i - (size_t)pl * P);
+                sm[i] = g[(size_t)pl * plane + (size_t)r0 * W + k];
+            }
+        }
+        cluster.sync();
+        int obs = 0;
+        while (obs < a.n_times && a.times[obs] <= a.t0) ++obs;
+        for (uint64_t t = a.t0; t < t_end; ++t) {
+            for (int s = 0; s < 2; ++s) {
+                if (have) {
+                    if (lt.V == 4) batch_half_step_v<4>(sm, lt, R, r0, remote_y[s], s, t);
+                    else if (lt.V == 2) batch_half_step_v<2>(sm, lt, R, r0, remote_y[s], s, t);
+                    else batch_half_step_v<1>(sm, lt, R, r0, remote_y[s], s, t);
+                }
+                cluster.sync();
+            }
+            while (obs < a.n_times && a.times[obs] == t + 1) {
+                ObsPartial *out = have ? a.partials + lt.part_off + (size_t)obs * lt.G + slot.part : nullptr;
+                batch_observe(cluster, sm, h0, have, lt, have ? slot.part : 0, R, base_rank, os, out);
+                ++obs;
+            }
+        }
+        if (have) {
+            uint32_t *g = a.state + lt.state_off;
+            const size_t plane = (size_t)lt.L * W;
+            for (uint32_t i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+                const uint32_t pl = (uint32_t)(i / P), k = (uint32_t)(i - (size_t)pl * P);
+                g[(size_t)pl * plane + (size_t)r0 * W + k] = sm[i];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One thread per (lattice, observation): add the G part partials in 128-bit integers.
+__global__ void k_batch_finalize(const BatchLattice *lat, int n_lat, const ObsPartial *part,
+                                 const uint64_t *times, int n_times, ObsDev *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_lat * n_times) return;
+    const int li = i / n_times, ob = i - li * n_times;
+    const BatchLattice lt = lat[li];
+    __int128 S1 = 0;
+    unsigned __int128 S2 = 0;
+    uint32_t flags = 0;
+    for (uint32_t g = 0; g < lt.G; ++g) {
+        const ObsPartial p = part[lt.part_off + (size_t)ob * lt.G + g];
+        S1 += p.s1;
+        S2 += ((unsigned __int128)p.s2_hi << 64) | p.s2_lo;
+        flags |= p.flags;
+    }
+    const unsigned __int128 N = (unsigned __int128)lt.L * lt.L;
+    const unsigned __int128 num = N * S2 - (unsigned __int128)(S1 * S1);
+    ObsDev o;
+    o.t = times[ob];
+    o.N = (uint64_t)N;
+    o.S1 = (int64_t)S1;
+    o.S2_lo = (uint64_t)S2;
+    o.S2_hi = (uint64_t)(S2 >> 64);
+    o.num_lo = (uint64_t)num;
+    o.num_hi = (uint64_t)(num >> 64);
+    o.w2 = 0.0;
+    o.status = flags ? -7 : 0;
+    o.reserved = (int32_t)flags;
+    out[i] = o;
+}
+
+// ---------------------------------------------------------------------------------------- host
+struct BatchPlan {
+    int C = 8;            // cluster size
+    int threads = 512;    // threads per CTA
+    size_t smem = 0;      // dynamic shared memory per CTA
+};
+
+size_t batch_part_smem(uint32_t L, uint32_t G)
+{
+    const uint32_t W = L / 64, R = L / G;
+    return 4 * (size_t)R * W * sizeof(uint32_t) + (size_t)R * sizeof(int32_t);
+}
+
+// Kernel attributes for a launch shape; call before launching or capturing.  The shared
+// memory limit only ever grows, so batches with different needs can coexist in one process.
+cudaError_t batch_prepare(int C, size_t smem)
+{
+    static std::mutex mu;
+    static size_t granted = 0;
+    static bool nonportable = false;
+    std::lock_guard<std::mutex> lock(mu);
+    auto kern = k_batch;
+    cudaError_t e = cudaSuccess;
+    if (smem > granted) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        granted = smem;
+    }
+    if (C > 8 && !nonportable) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) nonportable = true;
+    }
+    return e;
+}
+
+cudaError_t launch_batch(const BatchArgs &a, int n_clusters, int threads, size_t smem,
+                         cudaStream_t st)
+{
+    auto kern = k_batch;
+    cudaError_t e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_clusters * a.C), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, a);
+    count_launches(1);
+    return e;
+}
+
+cudaError_t batch_max_clusters(int C, int threads, size_t smem, int *out)
+{
+    auto kern = k_batch;
+    cudaError_t e = batch_prepare(C, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(out, kern, &cfg);
+}
+
+cudaError_t launch_batch_finalize(const BatchLattice *lat, int n_lat, const ObsPartial *part,
+                                  const uint64_t *times, int n_times, ObsDev *out, cudaStream_t st)
+{
+    const int n = n_lat * n_times;
+    k_batch_finalize<<<(n + 255) / 256, 256, 0, st>>>(lat, n_lat, part, times, n_times, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace sca
+
+// ------------------------------------------------------------------------------------ C ABI
+#include <algorithm>
+#include <cmath>
+#include <tuple>
+#include <string>
+#include <vector>
+
+#include "sca.h"
+
+namespace sca {
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *where);
+int make_rule(const sca_params &prm, Rule &R);
+
+constexpr uint32_t kBatchMaxL = 2048;          // observation teams span at most one warp
+constexpr int kBatchMaxObs = 64;
+constexpr size_t kBatchSmemCap = 200 * 1024;   // shared memory per CTA for one lattice part
+
+static uint32_t parts_needed(uint32_t L, int C)
+{
+    for (uint32_t G = 1; G <= (uint32_t)C; G <<= 1)
+        if (L % G == 0 && batch_part_smem(L, G) <= kBatchSmemCap && (L / G) >= 2) return G;
+    return 0;
+}
+}  // namespace sca
+
+using namespace sca;
+
+struct sca_batch {
+    std::vector<sca_params> P;
+    std::vector<BatchLattice> lat;     // host copy; G, part_off depend on the plan
+    std::vector<uint64_t> state_off;
+    uint32_t count = 0;
+    size_t state_words = 0;
+    uint32_t *state = nullptr;         // all lattices' canonical words
+    BatchLattice *lat_d = nullptr;
+    BatchSlot *slots_d = nullptr;
+    int n_units = 0;
+    uint32_t *counter = nullptr;
+    uint64_t *times_d = nullptr;
+    ObsPartial *part = nullptr;
+    size_t part_cap = 0;               // partial entries available
+    ObsDev *res = nullptr;             // count x kBatchMaxObs
+    ObsDev *res_h = nullptr;           // pinned copy
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t t = 0;
+    int C = 8, threads = 512, clusters = 0;
+    size_t smem = 0;
+    // captured run (reused while the observation times and start time repeat)
+    cudaGraphExec_t graph = nullptr;
+    std::vector<uint64_t> graph_times;
+    uint64_t graph_t0 = ~0ull;
+};
+
+static void batch_drop_graph(sca_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_times.clear();
+    b->graph_t0 = ~0ull;
+}
+
+// Pack lattices into cluster units: lattices of equal (L, G, rule cost) share units of C/G
+// lattices; units are ordered by decreasing estimated work so the dynamic queue balances.
+static int batch_plan(sca_batch *b, int C, int threads)
+{
+    const uint32_t n = b->count;
+    std::vector<uint32_t> G(n);
+    size_t smem = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        G[i] = parts_needed(b->lat[i].L, C);
+        if (G[i] == 0) return fail(SCA_EINVAL, "lattice too large for the batch cluster size");
+        smem = std::max(smem, batch_part_smem(b->lat[i].L, G[i]));
+    }
+    auto cost = [&](uint32_t i) {
+        const Rule &R = b->lat[i].R;
+        const double f = R.mode == 0 ? 1.0 : R.mode == 1 ? 1.0 + 1.5 * R.n_draws : 24.0;
+        return (double)b->lat[i].L * b->lat[i].L / G[i] * f;
+    };
+    // groups of interchangeable lattices: same parts, same size, same rule cost
+    std::vector<uint32_t> order(n);
+    for (uint32_t i = 0; i < n; ++i) order[i] = i;
+    auto key = [&](uint32_t i) { return std::make_tuple(G[i], b->lat[i].L, cost(i)); };
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return key(x) > key(y); });
+    struct Unit { double cost; std::vector<BatchSlot> s; };
+    std::vector<Unit> units;
+    for (size_t i = 0; i < order.size();) {
+        const uint32_t g = G[order[i]];
+        const uint32_t per = (uint32_t)C / g;
+        Unit u;
+        u.cost = cost(order[i]);
+        u.s.assign(C, BatchSlot{-1, 0});
+        const auto k0 = key(order[i]);
+        for (uint32_t k = 0; k < per && i < order.size() && key(order[i]) == k0; ++k, ++i)
+            for (uint32_t p = 0; p < g; ++p) u.s[k * g + p] = BatchSlot{(int32_t)order[i], (int32_t)p};
+        units.push_back(u);
+    }
+    std::stable_sort(units.begin(), units.end(), [](const Unit &x, const Unit &y) { return x.cost > y.cost; });
+    std::vector<BatchSlot> slots;
+    for (auto &u : units) slots.insert(slots.end(), u.s.begin(), u.s.end());
+    uint32_t part_off = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        b->lat[k].G = G[k];
+        b->lat[k].part_off = part_off;
+        part_off += G[k] * kBatchMaxObs;
+    }
+    int max_clusters = 0;
+    cudaError_t e = batch_max_clusters(C, threads, smem, &max_clusters);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();   // a refused shape must not surface at a later launch check
+        return cuda_fail(e, "cudaOccupancyMaxActiveClusters");
+    }
+    if (max_clusters < 1) return fail(SCA_EINVAL, "batch launch shape does not fit the GPU");
+    // device tables
+    if (b->slots_d) cudaFree(b->slots_d);
+    b->slots_d = nullptr;
+    e = cudaMalloc(&b->slots_d, slots.size() * sizeof(BatchSlot));
+    if (e != cudaSuccess) return fail(SCA_ENOMEM, "batch slot table");
+    e = cudaMemcpyAsync(b->slots_d, slots.data(), slots.size() * sizeof(BatchSlot),
+                        cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->lat_d, b->lat.data(), n * sizeof(BatchLattice), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch tables");
+    b->n_units = (int)units.size();
+    b->C = C;
+    b->threads = threads;
+    b->smem = smem;
+    b->clusters = std::min(max_clusters, b->n_units);
+    batch_drop_graph(b);
+    return SCA_OK;
+}
+
+extern "C" {
+
+int sca_batch_reset(sca_batch *b)
+{
+    if (!b) return fail(SCA_EINVAL, "NULL batch");
+    for (uint32_t i = 0; i < b->count; ++i) {
+        const size_t bytes = (size_t)b->lat[i].L * b->lat[i].L / 4;
+        char *p = (char *)(b->state + b->state_off[i]);
+        cudaError_t e = cudaMemsetAsync(p, 0x00, bytes / 2, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p + bytes / 2, 0xFF, bytes / 2, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    b->t = 0;
+    return SCA_OK;
+}
+
+void sca_batch_free(sca_batch *b);
+
+int sca_batch_init(const sca_params *params, uint32_t count, void *stream, sca_batch **out)
+{
+    if (!params || !out || count == 0) return fail(SCA_EINVAL, "NULL argument or empty batch");
+    *out = nullptr;
+    sca_batch *b = new sca_batch();
+    b->count = count;
+    b->P.assign(params, params + count);
+    b->lat.resize(count);
+    b->state_off.resize(count);
+    size_t words = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        const uint32_t L = params[i].L;
+        if (L < 128 || L % 64 != 0 || L > kBatchMaxL) {
+            delete b;
+            return fail(SCA_EINVAL, "batch lattices need L a multiple of 64 in [128, 2048]");
+        }
+        BatchLattice &lt = b->lat[i];
+        std::memset(&lt, 0, sizeof(lt));
+        int rc = make_rule(params[i], lt.R);
+        if (rc) { delete b; return rc; }
+        lt.L = L;
+        lt.W = L / 64;
+        lt.V = (lt.W % 4 == 0) ? 4 : (lt.W % 2 == 0) ? 2 : 1;
+        lt.state_off = words;
+        b->state_off[i] = words;
+        words += (size_t)L * L / 16;
+        words = (words + 63) & ~(size_t)63;          // 256-byte alignment per lattice
+    }
+    b->state_words = words;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaStreamCreate"); }
+        b->own_stream = true;
+    }
+    b->part_cap = 0;
+    for (uint32_t i = 0; i < count; ++i) b->part_cap += 8 * (size_t)kBatchMaxObs;   // G <= 8
+    cudaError_t e = cudaMalloc(&b->state, words * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b->lat_d, count * sizeof(BatchLattice));
+    if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b->times_d, kBatchMaxObs * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b->part, b->part_cap * sizeof(ObsPartial));
+    if (e == cudaSuccess) e = cudaMalloc(&b->res, (size_t)count * kBatchMaxObs * sizeof(ObsDev));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->res_h, (size_t)count * kBatchMaxObs * sizeof(ObsDev));
+    if (e != cudaSuccess) {
+        sca_batch_free(b);
+        return fail(SCA_ENOMEM, std::string("batch allocation: ") + cudaGetErrorString(e));
+    }
+    int rc = sca_batch_reset(b);
+    if (!rc) rc = batch_plan(b, 8, 512);
+    if (rc) { sca_batch_free(b); return rc; }
+    *out = b;
+    return SCA_OK;
+}
+
+int sca_batch_set_shape(sca_batch *b, int cluster, int threads)
+{
+    if (!b) return fail(SCA_EINVAL, "NULL batch");
+    if (!(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16) ||
+        !(threads == 128 || threads == 256 || threads == 384 || threads == 512))
+        return fail(SCA_EINVAL, "cluster must be 1, 2, 4, 8 or 16 and threads 128..512");
+    return batch_plan(b, cluster, threads);
+}
+
+int sca_batch_get_shape(const sca_batch *b, int *cluster, int *threads, int *clusters_launched,
+                        int *units)
+{
+    if (!b) return fail(SCA_EINVAL, "NULL batch");
+    if (cluster) *cluster = b->C;
+    if (threads) *threads = b->threads;
+    if (clusters_launched) *clusters_launched = b->clusters;
+    if (units) *units = b->n_units;
+    return SCA_OK;
+}
+
+static int batch_enqueue(sca_batch *b, uint32_t n)
+{
+    BatchArgs a;
+    a.state = b->state;
+    a.lat = b->lat_d;
+    a.slots = b->slots_d;
+    a.n_units = b->n_units;
+    a.C = b->C;
+    a.unit_counter = b->counter;
+    a.times = b->times_d;
+    a.n_times = (int)n;
+    a.t0 = b->t;
+    a.partials = b->part;
+    cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(uint32_t), b->stream);
+    if (e == cudaSuccess) e = launch_batch(a, b->clusters, b->threads, b->smem, b->stream);
+    if (e == cudaSuccess)
+        e = launch_batch_finalize(b->lat_d, (int)b->count, b->part, b->times_d, (int)n, b->res, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->res_h, b->res, (size_t)b->count * n * sizeof(ObsDev),
+                            cudaMemcpyDeviceToHost, b->stream);
+    return e == cudaSuccess ? SCA_OK : cuda_fail(e, "batch launch");
+}
+
+int sca_batch_run(sca_batch *b, const uint64_t *times, uint32_t n, sca_obs *out, double *ensemble_w2)
+{
+    if (!b || !times || n == 0) return fail(SCA_EINVAL, "NULL argument or no times");
+    if (n > (uint32_t)kBatchMaxObs) return fail(SCA_EINVAL, "at most 64 observation times per run");
+    uint64_t prev = b->t;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (times[i] <= prev) return fail(SCA_EINVAL, "times must be increasing and after the current MCS");
+        prev = times[i];
+    }
+    std::vector<uint64_t> tv(times, times + n);
+    int rc = SCA_OK;
+    if (!(b->graph && b->graph_t0 == b->t && b->graph_times == tv)) {
+        batch_drop_graph(b);
+        cudaError_t e = cudaMemcpyAsync(b->times_d, times, n * sizeof(uint64_t), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batch times");
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        rc = batch_enqueue(b, n);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { b->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+        b->graph_times = tv;
+        b->graph_t0 = b->t;
+    }
+    cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch run");
+    b->t = times[n - 1];
+    int first_bad = SCA_OK;
+    for (uint32_t ob = 0; ob < n; ++ob) {
+        double acc = 0.0;
+        for (uint32_t i = 0; i < b->count; ++i) {
+            sca_obs o;
+            std::memcpy(&o, &b->res_h[(size_t)i * n + ob], sizeof(o));
+            const double num = std::ldexp((double)o.num_hi, 64) + (double)o.num_lo;
+            o.w2 = num / ((double)o.N * (double)o.N);
+            if (o.status && !first_bad) first_bad = o.status;
+            acc += o.w2;
+            if (out) out[(size_t)i * n + ob] = o;
+        }
+        if (ensemble_w2) ensemble_w2[ob] = acc / b->count;
+    }
+    if (first_bad) return fail(first_bad, "a lattice's slopes do not close around the torus");
+    return SCA_OK;
+}
+
+int sca_batch_get_state(sca_batch *b, uint32_t index, uint32_t *host_words, size_t n_words)
+{
+    if (!b || !host_words || index >= b->count) return fail(SCA_EINVAL, "bad argument");
+    const size_t need = (size_t)b->lat[index].L * b->lat[index].L / 16;
+    if (n_words < need) return fail(SCA_EINVAL, "host buffer too small");
+    cudaError_t e = cudaMemcpyAsync(host_words, b->state + b->state_off[index], need * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? SCA_OK : cuda_fail(e, "sca_batch_get_state");
+}
+
+uint64_t sca_batch_time(const sca_batch *b) { return b ? b->t : 0; }
+
+int sca_batch_tune(sca_batch *b, uint32_t probe_mcs, int *best_cluster, int *best_threads)
+{
+    if (!b || probe_mcs == 0) return fail(SCA_EINVAL, "bad argument");
+    const int clusters[] = {8, 16, 4};
+    const int threads[] = {256, 384, 512};
+    double best = 1e300;
+    int bc = b->C, bt = b->threads;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(SCA_ECUDA, "cudaEventCreate");
+    for (int c : clusters) {
+        for (int t : threads) {
+            if (batch_plan(b, c, t) != SCA_OK) continue;      // shape does not fit: skip
+            int rc = sca_batch_reset(b);
+            if (rc) break;
+            const uint64_t tt = probe_mcs;
+            cudaEventRecord(e0, b->stream);
+            rc = sca_batch_run(b, &tt, 1, nullptr, nullptr);
+            cudaEventRecord(e1, b->stream);
+            if (rc) continue;
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                continue;
+            if (ms < best) { best = ms; bc = c; bt = t; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc = batch_plan(b, bc, bt);
+    if (!rc) rc = sca_batch_reset(b);
+    if (rc) return rc;
+    if (best_cluster) *best_cluster = bc;
+    if (best_threads) *best_threads = bt;
+    return SCA_OK;
+}
+
+void sca_batch_free(sca_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    cudaFree(b->state);
+    cudaFree(b->lat_d);
+    cudaFree(b->slots_d);
+    cudaFree(b->counter);
+    cudaFree(b->times_d);
+    cudaFree(b->part);
+    cudaFree(b->res);
+    if (b->res_h) cudaFreeHost(b->res_h);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

@@ -49,6 +49,18 @@ SIGNATURES = {
     "sca_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     "sca_free": (None, [C.c_void_p]),
+    "sca_batch_init": (C.c_int, [C.POINTER(sca_params), C.c_uint32, C.c_void_p,
+                                 C.POINTER(C.c_void_p)]),
+    "sca_batch_set_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "sca_batch_get_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "sca_batch_tune": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "sca_batch_run": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.c_uint32, C.c_void_p,
+                                C.c_void_p]),
+    "sca_batch_get_state": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t]),
+    "sca_batch_reset": (C.c_int, [C.c_void_p]),
+    "sca_batch_time": (C.c_uint64, [C.c_void_p]),
+    "sca_batch_free": (None, [C.c_void_p]),
     "sca_observe_noalloc": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint64, C.c_void_p,
                                       C.POINTER(sca_obs)]),
     "sca_strerror": (C.c_char_p, [C.c_int]),
@@ -243,6 +255,92 @@ class Sim:
     def close(self):
         if getattr(self, "_h", None):
             load().sca_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """An ensemble of independent lattices advanced by one persistent, graph-captured launch.
+
+    ``lattices``: iterable of dicts with keys L, p, q, seed and optional rng."""
+
+    def __init__(self, lattices, stream=None):
+        import torch
+        lib = load()
+        lat = list(lattices)
+        self.Ls = [int(d["L"]) for d in lat]
+        arr = (sca_params * len(lat))()
+        for i, d in enumerate(lat):
+            arr[i] = sca_params(L=int(d["L"]), rng=int(d.get("rng", RNG_AUTO)),
+                                seed=int(d["seed"]), p=float(d["p"]), q=float(d["q"]))
+        if stream is None:
+            stream = torch.cuda.Stream()
+        self.stream = stream
+        h = C.c_void_p()
+        check(lib.sca_batch_init(arr, len(lat), C.c_void_p(stream.cuda_stream), C.byref(h)),
+              "sca_batch_init")
+        self._h = h
+        self.count = len(lat)
+
+    def set_shape(self, cluster: int, threads: int):
+        check(load().sca_batch_set_shape(self._h, int(cluster), int(threads)), "sca_batch_set_shape")
+
+    def tune(self, probe_mcs: int = 32):
+        c, t = C.c_int(), C.c_int()
+        check(load().sca_batch_tune(self._h, int(probe_mcs), C.byref(c), C.byref(t)),
+              "sca_batch_tune")
+        return c.value, t.value
+
+    def shape(self):
+        c, t, n, u = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        check(load().sca_batch_get_shape(self._h, C.byref(c), C.byref(t), C.byref(n), C.byref(u)),
+              "sca_batch_get_shape")
+        return {"cluster": c.value, "threads": t.value, "clusters": n.value, "units": u.value}
+
+    def run(self, times, want_obs=True):
+        """Returns (obs[lattice][k], ensemble_w2[k])."""
+        times = [int(x) for x in times]
+        n = len(times)
+        arr = (C.c_uint64 * n)(*times)
+        out = (sca_obs * (self.count * n))() if want_obs else None
+        ens = (C.c_double * n)()
+        rc = load().sca_batch_run(self._h, arr, n, C.cast(out, C.c_void_p) if want_obs else None,
+                                  C.cast(ens, C.c_void_p))
+        if rc not in (OK, ESTATE):
+            check(rc, "sca_batch_run")
+        obs = None
+        if want_obs:
+            obs = [[Obs.from_c(out[i * n + k]) for k in range(n)] for i in range(self.count)]
+        return obs, list(ens)
+
+    def get_state(self, index: int) -> np.ndarray:
+        n = words_count(self.Ls[index])
+        out = np.empty(n, dtype=np.uint32)
+        check(load().sca_batch_get_state(self._h, int(index), out.ctypes.data_as(C.c_void_p), n),
+              "sca_batch_get_state")
+        return out
+
+    def reset(self):
+        check(load().sca_batch_reset(self._h), "sca_batch_reset")
+
+    @property
+    def t(self) -> int:
+        return int(load().sca_batch_time(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sca_batch_free(self._h)
             self._h = None
 
     def __del__(self):
