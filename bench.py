@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the p=1/2 context line")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble line")
+    ap.add_argument("--only", default="", choices=["", "batch"],
+                    help="run only the batched ensemble (sized by --batch-count/--batch-mcs)")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-mcs", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -207,6 +211,35 @@ def run_reference(a, rank, world):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def run_batch_only(a):
+    """The batched ensemble alone (first --batch-count lattices of the ensemble list,
+    --batch-mcs MCS), one timed run after one warm-up; prints one JSON line."""
+    import torch
+    import paper_1606_00310_gb300.sca as sca
+    from paper_1606_00310_gb300 import build, workloads
+    build.build()
+    sca.load()
+    ens = workloads.ensemble()[: a.batch_count]
+    times = workloads.log_times(a.batch_mcs)
+    stream = torch.cuda.Stream()
+    with sca.Batch(ens, stream=stream) as b:
+        b.run(times, want_obs=False)
+        b.reset()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, w2 = b.run(times, want_obs=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        shape = b.shape()
+    sites = sum(d["L"] ** 2 for d in ens)
+    print(json.dumps({"metric": METRIC, "value": sites * a.batch_mcs / (ms / 1000.0), "unit": UNIT,
+                      "workload": "batched ensemble, first %d lattices, %d MCS" % (len(ens), a.batch_mcs),
+                      "ms": ms, "shape": shape, "ensemble_w2_final": w2[-1]}), flush=True)
+
+
 def run_batched(sca, torch, stream, dev, L_single, peak):
     """Batched ensemble: 4096 lattices, L uniform in {128..2048}, half (1, 0), half (7/8, 1/8),
     4096 MCS with W^2 at 2^0..2^12, one persistent graph-captured launch per run.  Compared
@@ -418,6 +451,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return
+    if a.only == "batch":
+        run_batch_only(a)
         return
     if world > 1:
         import torch

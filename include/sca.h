@@ -196,6 +196,12 @@ int sca_batch_tune(sca_batch *b, uint32_t probe_mcs, int *best_cluster, int *bes
 int sca_batch_run(sca_batch *b, const uint64_t *times, uint32_t n, sca_obs *out,
                   double *ensemble_w2);
 
+/* Diagnostics of the last run: for each work unit (units are ordered by decreasing estimated
+ * cost), the device clock (ns) when its cluster started and finished it, and the index of its
+ * first lattice.  n must be at least the unit count (sca_batch_get_shape).  Synchronises. */
+int sca_batch_unit_times(sca_batch *b, uint64_t *start_ns, uint64_t *end_ns,
+                         int32_t *first_lattice, uint32_t n);
+
 /* Canonical words of lattice `index` (4 * L * L/64 words) to host memory; synchronises. */
 int sca_batch_get_state(sca_batch *b, uint32_t index, uint32_t *host_words, size_t n_words);
 

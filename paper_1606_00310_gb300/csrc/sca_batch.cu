@@ -30,7 +30,8 @@ struct BatchLattice {
 
 struct BatchSlot {
     int32_t lattice;     // -1: this CTA idles in the unit
-    int32_t part;
+    int16_t part;
+    int16_t unit_G;      // parts per lattice in this unit (same for every slot of the unit)
 };
 
 struct BatchArgs {
@@ -43,27 +44,62 @@ struct BatchArgs {
     int n_times;
     uint64_t t0;
     ObsPartial *partials;
+    uint64_t *unit_ns;         // per unit: start and end time (globaltimer, ns)
 };
 
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int V>
+__device__ __forceinline__ void ldv(const uint32_t *p, uint32_t (&r)[V])
+{
+    if constexpr (V == 4) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(p);
+        r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
+    } else if constexpr (V == 2) {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        r[0] = q.x; r[1] = q.y;
+    } else {
+        r[0] = *p;
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void stv(uint32_t *p, const uint32_t (&r)[V])
+{
+    if constexpr (V == 4) {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(r[0], r[1], r[2], r[3]);
+    } else if constexpr (V == 2) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(r[0], r[1]);
+    } else {
+        *p = r[0];
+    }
+}
+
 // One item of a half-step in shared memory: V words of one row.  In a shifted row the mask
-// enters the neighbour sublattice's sx- one bit up; the first word of every item is updated
-// with a shared-memory atomic xor because the item to its left xors its carry bit into it.
-template <int V, int MODE>
+// enters the neighbour sublattice's sx- one bit up, and the top bit of the item's last word
+// belongs in bit 0 of the next item's first word.  That bit is not written here: it goes to
+// carry[] and the owner of that word applies it when it next loads the word as its own sx-
+// (the next half-step, which updates that sublattice), so no two threads ever write one word.
+template <int V, int MODE, int ND>
 __device__ __forceinline__ void batch_item(uint32_t *own_x, uint32_t *own_y, uint32_t *nb_x,
                                            uint32_t *nb_yn, uint32_t j, uint32_t W, bool shifted,
-                                           const Rule &R, uint32_t y, uint32_t L, uint64_t t, int s)
+                                           const Rule &R, const uint32_t *rk, uint32_t y, uint32_t L,
+                                           uint64_t t, int s, uint32_t carry_in, uint8_t *carry_out)
 {
     uint32_t xm[V], ym[V], nx[V], ny[V], xpl[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        xm[v] = own_x[j + v];
-        ym[v] = own_y[j + v];
-        nx[v] = nb_x[j + v];
-        ny[v] = nb_yn[j + v];
-    }
+    ldv<V>(own_x + j, xm);                // one 128-bit access per plane for V = 4: consecutive
+    ldv<V>(own_y + j, ym);                // threads touch consecutive 16-byte chunks, so the
+    ldv<V>(nb_x + j, nx);                 // accesses are free of bank conflicts
+    ldv<V>(nb_yn + j, ny);
+    xm[0] ^= carry_in;                    // pending carry of the previous half-step
     if (shifted) {
         const uint32_t jn = (j + V == W) ? 0u : j + V;
-        const uint32_t next = nb_x[jn];   // bit 0 only; nobody changes it before our own xor
+        const uint32_t next = nb_x[jn];   // bit 0 only: settled, its pending carry was applied
 #pragma unroll
         for (int v = 0; v < V; ++v) xpl[v] = (nx[v] >> 1) | ((v + 1 < V ? nx[(v + 1) % V] : next) << 31);
     } else {
@@ -78,36 +114,43 @@ __device__ __forceinline__ void batch_item(uint32_t *own_x, uint32_t *own_y, uin
             xiq[v] = R.Pq ? 0xFFFFFFFFu : 0u;
         }
     } else if constexpr (MODE == 1) {
-        xi_dyadic<V>(R, (uint64_t)y * W + j, t, s, xip, xiq);
+        xi_dyadic_any<V, ND>(R, rk, (uint64_t)y * W + j, t, s, xip, xiq);
     } else {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const uint32_t need = eligible(xm[v], ym[v], xpl[v], ny[v]);
-            xi_uniform_word(R, (uint64_t)y * (L / 2) + 32u * (j + v), t, s, need, xip[v], xiq[v]);
+            xi_uniform_word(R, rk, (uint64_t)y * (L / 2) + 32u * (j + v), t, s, need, xip[v], xiq[v]);
         }
     }
     uint32_t m[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         m[v] = update_mask(xm[v], ym[v], xpl[v], ny[v], xip[v], xiq[v]);
-        own_x[j + v] = xm[v] ^ m[v];
-        own_y[j + v] = ym[v] ^ m[v];
-        nb_yn[j + v] = ny[v] ^ m[v];
+        xm[v] ^= m[v];
+        ym[v] ^= m[v];
+        ny[v] ^= m[v];
     }
+    stv<V>(own_x + j, xm);
+    stv<V>(own_y + j, ym);
+    stv<V>(nb_yn + j, ny);
     if (!shifted) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) nb_x[j + v] = nx[v] ^ m[v];
+        for (int v = 0; v < V; ++v) nx[v] ^= m[v];
+        *carry_out = 0;
     } else {
-        atomicXor(&nb_x[j], m[0] << 1);
 #pragma unroll
-        for (int v = 1; v < V; ++v) nb_x[j + v] = nx[v] ^ ((m[v] << 1) | (m[v - 1] >> 31));
-        atomicXor(&nb_x[(j + V == W) ? 0u : j + V], m[V - 1] >> 31);
+        for (int v = 0; v < V; ++v) nx[v] ^= (m[v] << 1) | (v > 0 ? (m[(v + V - 1) % V] >> 31) : 0u);
+        *carry_out = (uint8_t)(m[V - 1] >> 31);
     }
+    stv<V>(nb_x + j, nx);
 }
 
-template <int V, int MODE>
-__device__ void batch_half_step(uint32_t *sm, const BatchLattice &lt, uint32_t R, uint32_t r0,
-                                uint32_t *remote_nb_y, int s, uint64_t t)
+// Carries live in two byte arrays, one byte per item (row-major, W / V items per row): the
+// half-step of sublattice s reads the carries pending for its own sx- words from cbuf[s] and
+// writes the ones it produces into cbuf[s ^ 1], so reads and writes never meet.
+template <int V, int MODE, int ND>
+__device__ void batch_half_step(uint32_t *sm, uint8_t *cbuf, const BatchLattice &lt, const uint32_t *rk,
+                                uint32_t R, uint32_t r0, uint32_t *remote_nb_y, int s, uint64_t t)
 {
     const uint32_t W = lt.W;
     const size_t P = (size_t)R * W;
@@ -117,23 +160,47 @@ __device__ void batch_half_step(uint32_t *sm, const BatchLattice &lt, uint32_t R
     uint32_t *nby = sm + (size_t)((s ^ 1) * 2 + 1) * P;
     const uint32_t per_row = W / V;
     const uint32_t items = R * per_row;
+    const uint8_t *c_rd = cbuf + (size_t)s * items;
+    uint8_t *c_wr = cbuf + (size_t)(s ^ 1) * items;
+    const bool pow2 = (per_row & (per_row - 1)) == 0;
+    const uint32_t sh = pow2 ? (uint32_t)__ffs(per_row) - 1 : 0;
     for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
-        const uint32_t r = it / per_row;
-        const uint32_t j = (it - r * per_row) * V;
+        const uint32_t r = pow2 ? it >> sh : it / per_row;
+        const uint32_t q = it - r * per_row;
         const uint32_t y = r0 + r;
         uint32_t *nyn = (r + 1 < R) ? nby + (size_t)(r + 1) * W : remote_nb_y;
-        batch_item<V, MODE>(own_x + (size_t)r * W, own_y + (size_t)r * W, nbx + (size_t)r * W, nyn,
-                            j, W, ((uint32_t)s + y) & 1u, lt.R, y, lt.L, t, s);
+        batch_item<V, MODE, ND>(own_x + (size_t)r * W, own_y + (size_t)r * W, nbx + (size_t)r * W, nyn,
+                            q * V, W, ((uint32_t)s + y) & 1u, lt.R, rk, y, lt.L, t, s, c_rd[it],
+                            &c_wr[r * per_row + (q + 1 == per_row ? 0 : q + 1)]);
     }
 }
 
 template <int V>
-__device__ void batch_half_step_v(uint32_t *sm, const BatchLattice &lt, uint32_t R, uint32_t r0,
-                                  uint32_t *remote_nb_y, int s, uint64_t t)
+__device__ void batch_half_step_v(uint32_t *sm, uint8_t *cbuf, const BatchLattice &lt, const uint32_t *rk,
+                                  uint32_t R, uint32_t r0, uint32_t *remote_nb_y, int s, uint64_t t)
 {
-    if (lt.R.mode == 0) batch_half_step<V, 0>(sm, lt, R, r0, remote_nb_y, s, t);
-    else if (lt.R.mode == 1) batch_half_step<V, 1>(sm, lt, R, r0, remote_nb_y, s, t);
-    else batch_half_step<V, 2>(sm, lt, R, r0, remote_nb_y, s, t);
+    if (lt.R.mode == 0) batch_half_step<V, 0, 0>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t);
+    else if (lt.R.mode == 1) {
+        switch (lt.R.n_draws) {
+        case 1: batch_half_step<V, 1, 1>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t); break;
+        case 2: batch_half_step<V, 1, 2>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t); break;
+        case 3: batch_half_step<V, 1, 3>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t); break;
+        case 4: batch_half_step<V, 1, 4>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t); break;
+        default: batch_half_step<V, 1, 0>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t); break;
+        }
+    } else batch_half_step<V, 2, 0>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t);
+}
+
+// Apply the carries pending after an odd half-step (they belong to sublattice 0's sx- words,
+// read from cbuf[0]) and clear them; needed before the state is read as a whole.
+__device__ void batch_flush_carry(uint32_t *sm, uint8_t *cbuf, const BatchLattice &lt, uint32_t R)
+{
+    const uint32_t W = lt.W, V = lt.V, per_row = W / V, items = R * per_row;
+    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+        const uint32_t r = it / per_row, q = it - r * per_row;
+        sm[(size_t)r * W + q * V] ^= cbuf[it];      // plane 0 = sublattice 0, sx-
+        cbuf[it] = 0;
+    }
 }
 
 __device__ __forceinline__ int64_t warp_scan_incl(int64_t v, int width)
@@ -174,8 +241,8 @@ struct ObsShared {
 };
 
 // Roughness partial of this CTA's rows at one observation (all CTAs of the cluster call it).
-__device__ void batch_observe(cg::cluster_group &cluster, uint32_t *sm, int32_t *h0, bool have,
-                              const BatchLattice &lt, int part, uint32_t R, int base_rank,
+__device__ void batch_observe(cg::cluster_group &cluster, bool multi, uint32_t *sm, int32_t *h0,
+                              bool have, const BatchLattice &lt, int part, uint32_t R, int base_rank,
                               ObsShared &os, ObsPartial *out)
 {
     const uint32_t W = have ? lt.W : 1;
@@ -203,7 +270,8 @@ __device__ void batch_observe(cg::cluster_group &cluster, uint32_t *sm, int32_t 
         os.colsum = tot;
         os.colsum_all = tot_all;
     }
-    cluster.sync();
+    if (multi) cluster.sync();
+    else __syncthreads();
     int64_t offset = 0;
     if (have) {
         for (int q = 0; q < part; ++q)
@@ -285,7 +353,8 @@ __device__ void batch_observe(cg::cluster_group &cluster, uint32_t *sm, int32_t 
         out->s2_hi = 0;
         out->flags = os.flag;
     }
-    cluster.sync();   // neighbours are done reading colsum before it is reused
+    if (multi) cluster.sync();   // the other parts are done reading colsum before it is reused
+    else __syncthreads();
 }
 
 __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a)
@@ -293,6 +362,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a)
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ int s_unit;
     __shared__ ObsShared os;
+    __shared__ uint32_t s_rk[20];      // Philox round keys of this CTA's lattice
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const uint64_t t_end = a.times[a.n_times - 1];
@@ -303,8 +373,12 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a)
         const int unit = *cluster.map_shared_rank(&s_unit, 0);
         cluster.sync();
         if (unit >= a.n_units) break;
+        if (rank == 0 && threadIdx.x == 0) a.unit_ns[2 * unit] = global_ns();
         const BatchSlot slot = a.slots[(size_t)unit * a.C + rank];
         const bool have = slot.lattice >= 0;
+        // lattices split over CTAs need cluster barriers; a unit of one-CTA lattices runs each
+        // CTA on its own with block barriers (the choice is the same for every CTA of the unit)
+        const bool multi = slot.unit_G > 1;
         BatchLattice lt;
         if (have) lt = a.lat[slot.lattice];
         else { lt.L = 64; lt.W = 1; lt.G = 1; lt.V = 1; }
@@ -313,7 +387,9 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a)
         const uint32_t r0 = have ? (uint32_t)slot.part * R : 0;
         const int base_rank = rank - (have ? slot.part : 0);
         const size_t P = (size_t)R * W;
+        const uint32_t items = have ? R * (W / lt.V) : 0;
         int32_t *h0 = reinterpret_cast<int32_t *>(sm + 4 * P);
+        uint8_t *cbuf = reinterpret_cast<uint8_t *>(h0 + R);
         // the sy- plane of the other sublattice, first row of the next part (periodic)
         uint32_t *remote_y[2] = {nullptr, nullptr};
         if (have) {
@@ -326,26 +402,36 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a)
                 const uint32_t pl = (uint32_t)(i / P), k = (uint32_t)(i - (size_t)pl * P);
                 sm[i] = g[(size_t)pl * plane + (size_t)r0 * W + k];
             }
+            for (uint32_t i = threadIdx.x; i < 2 * items; i += blockDim.x) cbuf[i] = 0;
+            if (threadIdx.x < 20) s_rk[threadIdx.x] = a.lat[slot.lattice].R.rk[threadIdx.x];
         }
-        cluster.sync();
+        if (multi) cluster.sync();
+        else __syncthreads();
         int obs = 0;
         while (obs < a.n_times && a.times[obs] <= a.t0) ++obs;
         for (uint64_t t = a.t0; t < t_end; ++t) {
             for (int s = 0; s < 2; ++s) {
                 if (have) {
-                    if (lt.V == 4) batch_half_step_v<4>(sm, lt, R, r0, remote_y[s], s, t);
-                    else if (lt.V == 2) batch_half_step_v<2>(sm, lt, R, r0, remote_y[s], s, t);
-                    else batch_half_step_v<1>(sm, lt, R, r0, remote_y[s], s, t);
+                    if (lt.V == 4) batch_half_step_v<4>(sm, cbuf, lt, s_rk, R, r0, remote_y[s], s, t);
+                    else if (lt.V == 2) batch_half_step_v<2>(sm, cbuf, lt, s_rk, R, r0, remote_y[s], s, t);
+                    else batch_half_step_v<1>(sm, cbuf, lt, s_rk, R, r0, remote_y[s], s, t);
                 }
-                cluster.sync();
+                if (multi) cluster.sync();
+                else __syncthreads();
             }
-            while (obs < a.n_times && a.times[obs] == t + 1) {
-                ObsPartial *out = have ? a.partials + lt.part_off + (size_t)obs * lt.G + slot.part : nullptr;
-                batch_observe(cluster, sm, h0, have, lt, have ? slot.part : 0, R, base_rank, os, out);
-                ++obs;
+            if (obs < a.n_times && a.times[obs] == t + 1) {
+                if (have) batch_flush_carry(sm, cbuf, lt, R);
+                __syncthreads();
+                while (obs < a.n_times && a.times[obs] == t + 1) {
+                    ObsPartial *out = have ? a.partials + lt.part_off + (size_t)obs * lt.G + slot.part : nullptr;
+                    batch_observe(cluster, multi, sm, h0, have, lt, have ? slot.part : 0, R, base_rank, os, out);
+                    ++obs;
+                }
             }
         }
         if (have) {
+            batch_flush_carry(sm, cbuf, lt, R);
+            __syncthreads();
             uint32_t *g = a.state + lt.state_off;
             const size_t plane = (size_t)lt.L * W;
             for (uint32_t i = threadIdx.x; i < 4 * P; i += blockDim.x) {
@@ -354,6 +440,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a)
             }
         }
         __syncthreads();
+        if (rank == 0 && threadIdx.x == 0) a.unit_ns[2 * unit + 1] = global_ns();
     }
 }
 
@@ -400,7 +487,9 @@ struct BatchPlan {
 size_t batch_part_smem(uint32_t L, uint32_t G)
 {
     const uint32_t W = L / 64, R = L / G;
-    return 4 * (size_t)R * W * sizeof(uint32_t) + (size_t)R * sizeof(int32_t);
+    const uint32_t V = (W % 4 == 0) ? 4 : (W % 2 == 0) ? 2 : 1;
+    return 4 * (size_t)R * W * sizeof(uint32_t) + (size_t)R * sizeof(int32_t) +
+           2 * (size_t)R * (W / V);
 }
 
 // Kernel attributes for a launch shape; call before launching or capturing.  The shared
@@ -493,12 +582,12 @@ int make_rule(const sca_params &prm, Rule &R);
 
 constexpr uint32_t kBatchMaxL = 2048;          // observation teams span at most one warp
 constexpr int kBatchMaxObs = 64;
-constexpr size_t kBatchSmemCap = 200 * 1024;   // shared memory per CTA for one lattice part
+constexpr size_t kBatchSmemCap = 200 * 1024;   // default shared memory per CTA for one part
 
-static uint32_t parts_needed(uint32_t L, int C)
+static uint32_t parts_needed(uint32_t L, int C, size_t cap)
 {
     for (uint32_t G = 1; G <= (uint32_t)C; G <<= 1)
-        if (L % G == 0 && batch_part_smem(L, G) <= kBatchSmemCap && (L / G) >= 2) return G;
+        if (L % G == 0 && batch_part_smem(L, G) <= cap && (L / G) >= 2) return G;
     return 0;
 }
 }  // namespace sca
@@ -517,6 +606,8 @@ struct sca_batch {
     int n_units = 0;
     uint32_t *counter = nullptr;
     uint64_t *times_d = nullptr;
+    uint64_t *unit_ns = nullptr;       // 2 per unit (capacity: one unit per lattice)
+    std::vector<int32_t> unit_first;   // first lattice of each unit (host copy)
     ObsPartial *part = nullptr;
     size_t part_cap = 0;               // partial entries available
     ObsDev *res = nullptr;             // count x kBatchMaxObs
@@ -525,7 +616,7 @@ struct sca_batch {
     bool own_stream = false;
     uint64_t t = 0;
     int C = 8, threads = 512, clusters = 0;
-    size_t smem = 0;
+    size_t smem = 0, cap = 0;
     // captured run (reused while the observation times and start time repeat)
     cudaGraphExec_t graph = nullptr;
     std::vector<uint64_t> graph_times;
@@ -542,13 +633,13 @@ static void batch_drop_graph(sca_batch *b)
 
 // Pack lattices into cluster units: lattices of equal (L, G, rule cost) share units of C/G
 // lattices; units are ordered by decreasing estimated work so the dynamic queue balances.
-static int batch_plan(sca_batch *b, int C, int threads)
+static int batch_plan(sca_batch *b, int C, int threads, size_t cap = kBatchSmemCap)
 {
     const uint32_t n = b->count;
     std::vector<uint32_t> G(n);
     size_t smem = 0;
     for (uint32_t i = 0; i < n; ++i) {
-        G[i] = parts_needed(b->lat[i].L, C);
+        G[i] = parts_needed(b->lat[i].L, C, cap);
         if (G[i] == 0) return fail(SCA_EINVAL, "lattice too large for the batch cluster size");
         smem = std::max(smem, batch_part_smem(b->lat[i].L, G[i]));
     }
@@ -569,15 +660,19 @@ static int batch_plan(sca_batch *b, int C, int threads)
         const uint32_t per = (uint32_t)C / g;
         Unit u;
         u.cost = cost(order[i]);
-        u.s.assign(C, BatchSlot{-1, 0});
+        u.s.assign(C, BatchSlot{-1, 0, (int16_t)g});
         const auto k0 = key(order[i]);
         for (uint32_t k = 0; k < per && i < order.size() && key(order[i]) == k0; ++k, ++i)
-            for (uint32_t p = 0; p < g; ++p) u.s[k * g + p] = BatchSlot{(int32_t)order[i], (int32_t)p};
+            for (uint32_t p = 0; p < g; ++p) u.s[k * g + p] = BatchSlot{(int32_t)order[i], (int16_t)p, (int16_t)g};
         units.push_back(u);
     }
     std::stable_sort(units.begin(), units.end(), [](const Unit &x, const Unit &y) { return x.cost > y.cost; });
     std::vector<BatchSlot> slots;
-    for (auto &u : units) slots.insert(slots.end(), u.s.begin(), u.s.end());
+    b->unit_first.clear();
+    for (auto &u : units) {
+        slots.insert(slots.end(), u.s.begin(), u.s.end());
+        b->unit_first.push_back(u.s[0].lattice);
+    }
     uint32_t part_off = 0;
     for (uint32_t k = 0; k < n; ++k) {
         b->lat[k].G = G[k];
@@ -603,6 +698,7 @@ static int batch_plan(sca_batch *b, int C, int threads)
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch tables");
     b->n_units = (int)units.size();
+    b->cap = cap;
     b->C = C;
     b->threads = threads;
     b->smem = smem;
@@ -671,6 +767,7 @@ int sca_batch_init(const sca_params *params, uint32_t count, void *stream, sca_b
     if (e == cudaSuccess) e = cudaMalloc(&b->lat_d, count * sizeof(BatchLattice));
     if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&b->times_d, kBatchMaxObs * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b->unit_ns, 2 * (size_t)count * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMalloc(&b->part, b->part_cap * sizeof(ObsPartial));
     if (e == cudaSuccess) e = cudaMalloc(&b->res, (size_t)count * kBatchMaxObs * sizeof(ObsDev));
     if (e == cudaSuccess) e = cudaMallocHost(&b->res_h, (size_t)count * kBatchMaxObs * sizeof(ObsDev));
@@ -718,6 +815,7 @@ static int batch_enqueue(sca_batch *b, uint32_t n)
     a.n_times = (int)n;
     a.t0 = b->t;
     a.partials = b->part;
+    a.unit_ns = b->unit_ns;
     cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(uint32_t), b->stream);
     if (e == cudaSuccess) e = launch_batch(a, b->clusters, b->threads, b->smem, b->stream);
     if (e == cudaSuccess)
@@ -792,39 +890,59 @@ int sca_batch_get_state(sca_batch *b, uint32_t index, uint32_t *host_words, size
 
 uint64_t sca_batch_time(const sca_batch *b) { return b ? b->t : 0; }
 
+int sca_batch_unit_times(sca_batch *b, uint64_t *start_ns, uint64_t *end_ns, int32_t *first_lattice,
+                         uint32_t n)
+{
+    if (!b) return fail(SCA_EINVAL, "NULL batch");
+    const uint32_t u = (uint32_t)b->n_units;
+    if (n < u) return fail(SCA_EINVAL, "buffers shorter than the unit count");
+    std::vector<uint64_t> ns(2 * (size_t)u);
+    cudaError_t e = cudaMemcpyAsync(ns.data(), b->unit_ns, ns.size() * sizeof(uint64_t),
+                                    cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sca_batch_unit_times");
+    for (uint32_t i = 0; i < u; ++i) {
+        if (start_ns) start_ns[i] = ns[2 * i];
+        if (end_ns) end_ns[i] = ns[2 * i + 1];
+        if (first_lattice) first_lattice[i] = b->unit_first[i];
+    }
+    return SCA_OK;
+}
+
 int sca_batch_tune(sca_batch *b, uint32_t probe_mcs, int *best_cluster, int *best_threads)
 {
     if (!b || probe_mcs == 0) return fail(SCA_EINVAL, "bad argument");
-    const int clusters[] = {8, 16, 4};
-    const int threads[] = {256, 384, 512};
+    struct Shape { int c, t; size_t cap; };
+    // one CTA per SM with up to 200 KiB each, or two per SM with up to 100 KiB (more CTAs
+    // per lattice, hence larger clusters)
+    const Shape shapes[] = {{8, 512, 200 * 1024}, {8, 384, 200 * 1024}, {8, 256, 200 * 1024},
+                            {16, 256, 100 * 1024}, {16, 512, 200 * 1024}, {4, 512, 200 * 1024}};
     double best = 1e300;
-    int bc = b->C, bt = b->threads;
+    Shape bs{b->C, b->threads, b->cap};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(SCA_ECUDA, "cudaEventCreate");
-    for (int c : clusters) {
-        for (int t : threads) {
-            if (batch_plan(b, c, t) != SCA_OK) continue;      // shape does not fit: skip
-            int rc = sca_batch_reset(b);
-            if (rc) break;
-            const uint64_t tt = probe_mcs;
-            cudaEventRecord(e0, b->stream);
-            rc = sca_batch_run(b, &tt, 1, nullptr, nullptr);
-            cudaEventRecord(e1, b->stream);
-            if (rc) continue;
-            float ms = 0.f;
-            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-                continue;
-            if (ms < best) { best = ms; bc = c; bt = t; }
-        }
+    for (const Shape &sh : shapes) {
+        if (batch_plan(b, sh.c, sh.t, sh.cap) != SCA_OK) continue;   // shape does not fit: skip
+        int rc = sca_batch_reset(b);
+        if (rc) break;
+        const uint64_t tt = probe_mcs;
+        cudaEventRecord(e0, b->stream);
+        rc = sca_batch_run(b, &tt, 1, nullptr, nullptr);
+        cudaEventRecord(e1, b->stream);
+        if (rc) continue;
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            continue;
+        if (ms < best) { best = ms; bs = sh; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int rc = batch_plan(b, bc, bt);
+    int rc = batch_plan(b, bs.c, bs.t, bs.cap);
     if (!rc) rc = sca_batch_reset(b);
     if (rc) return rc;
-    if (best_cluster) *best_cluster = bc;
-    if (best_threads) *best_threads = bt;
+    if (best_cluster) *best_cluster = bs.c;
+    if (best_threads) *best_threads = bs.t;
     return SCA_OK;
 }
 
@@ -838,6 +956,7 @@ void sca_batch_free(sca_batch *b)
     cudaFree(b->slots_d);
     cudaFree(b->counter);
     cudaFree(b->times_d);
+    cudaFree(b->unit_ns);
     cudaFree(b->part);
     cudaFree(b->res);
     if (b->res_h) cudaFreeHost(b->res_h);

@@ -126,7 +126,7 @@ __device__ __forceinline__ void sts(uint32_t *p, const uint32_t (&r)[V])
 // nb_yn: the other sublattice's sy- words of the next row (sy+).  In a shifted row the mask
 // enters nb_x one bit up and the top bit of each thread's last word is published in carry[]
 // for the owner of the next word, who applies it after the next barrier.
-template <int V, int MODE>
+template <int V, int MODE, int ND>
 __device__ __forceinline__ void half_row(uint32_t *own_x, uint32_t *own_y, uint32_t *nb_x,
                                          uint32_t *nb_yn, bool shifted, int lane, int T,
                                          uint32_t W, const Rule &R, uint32_t y, uint32_t L,
@@ -154,12 +154,12 @@ __device__ __forceinline__ void half_row(uint32_t *own_x, uint32_t *own_y, uint3
             xiq[v] = R.Pq ? 0xFFFFFFFFu : 0u;
         }
     } else if constexpr (MODE == 1) {
-        xi_dyadic<V>(R, (uint64_t)y * W + j, t, s, xip, xiq);
+        xi_dyadic_any<V, ND>(R, R.rk, (uint64_t)y * W + j, t, s, xip, xiq);
     } else {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const uint32_t need = eligible(xm[v], ym[v], xpl[v], ny[v]);
-            xi_uniform_word(R, (uint64_t)y * (L / 2) + 32u * (j + v), t, s, need, xip[v], xiq[v]);
+            xi_uniform_word(R, R.rk, (uint64_t)y * (L / 2) + 32u * (j + v), t, s, need, xip[v], xiq[v]);
         }
     }
     uint32_t m[V];
@@ -185,7 +185,7 @@ __device__ __forceinline__ void half_row(uint32_t *own_x, uint32_t *own_y, uint3
     (void)T;
 }
 
-template <int V, int MODE>
+template <int V, int MODE, int ND>
 __global__ void __launch_bounds__(512) k_fused_mcs(const FusedArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -242,13 +242,13 @@ __global__ void __launch_bounds__(512) k_fused_mcs(const FusedArgs a)
     auto even_row = [&](int r) {      // sublattice 0 at row r, reads rows r and r+1
         const uint32_t y = gy(r);
         uint32_t *cur = slot(r), *nxt = slot(r + 1);
-        half_row<V, MODE>(cur, cur + W, cur + 2 * W, nxt + 3 * W, (y & 1u) != 0, lane, T, W, a.R,
+        half_row<V, MODE, ND>(cur, cur + W, cur + 2 * W, nxt + 3 * W, (y & 1u) != 0, lane, T, W, a.R,
                           y, L, a.t, 0, cE);
     };
     auto odd_row = [&](int r) {       // sublattice 1 at row r, reads rows r and r+1
         const uint32_t y = gy(r);
         uint32_t *cur = slot(r), *nxt = slot(r + 1);
-        half_row<V, MODE>(cur + 2 * W, cur + 3 * W, cur, nxt + W, (y & 1u) == 0, lane, T, W, a.R,
+        half_row<V, MODE, ND>(cur + 2 * W, cur + 3 * W, cur, nxt + W, (y & 1u) == 0, lane, T, W, a.R,
                           y, L, a.t, 1, cO);
     };
     auto prev_lane = [&]() { return lane == 0 ? T - 1 : lane - 1; };
@@ -326,10 +326,10 @@ size_t fused_smem_bytes(uint32_t L)
     return ring_off + (size_t)kRing * 4 * W * sizeof(uint32_t);
 }
 
-template <int V, int MODE>
+template <int V, int MODE, int ND>
 static cudaError_t launch_fused_v(FusedArgs a, size_t smem, cudaStream_t st)
 {
-    auto kern = k_fused_mcs<V, MODE>;
+    auto kern = k_fused_mcs<V, MODE, ND>;
     static int configured_smem = 0;
     if ((int)smem > configured_smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -358,14 +358,22 @@ cudaError_t launch_fused_mcs(const uint32_t *src, uint32_t *dst, uint32_t L, uin
     FusedArgs a{src, dst, L, W, (int)(W / V), 0, t, R, err};
     const size_t smem = fused_smem_bytes(L);
     const int mode = (int)R.mode;
-    if (V == 4) {
-        if (mode == 0) return launch_fused_v<4, 0>(a, smem, st);
-        if (mode == 1) return launch_fused_v<4, 1>(a, smem, st);
-        return launch_fused_v<4, 2>(a, smem, st);
+#define SCA_FUSED_V(VV)                                                         \
+    if (V == VV) {                                                              \
+        if (mode == 0) return launch_fused_v<VV, 0, 0>(a, smem, st);            \
+        if (mode == 2) return launch_fused_v<VV, 2, 0>(a, smem, st);            \
+        switch (R.n_draws) {                                                    \
+        case 1: return launch_fused_v<VV, 1, 1>(a, smem, st);                   \
+        case 2: return launch_fused_v<VV, 1, 2>(a, smem, st);                   \
+        case 3: return launch_fused_v<VV, 1, 3>(a, smem, st);                   \
+        case 4: return launch_fused_v<VV, 1, 4>(a, smem, st);                   \
+        default: return launch_fused_v<VV, 1, 0>(a, smem, st);                  \
+        }                                                                       \
     }
-    if (mode == 0) return launch_fused_v<1, 0>(a, smem, st);
-    if (mode == 1) return launch_fused_v<1, 1>(a, smem, st);
-    return launch_fused_v<1, 2>(a, smem, st);
+    SCA_FUSED_V(4)
+    SCA_FUSED_V(1)
+#undef SCA_FUSED_V
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace sca

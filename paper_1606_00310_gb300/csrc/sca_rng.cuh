@@ -26,6 +26,22 @@ __device__ __forceinline__ Ctr4 philox4x32_10(Ctr4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// The same ten rounds with the key schedule precomputed: rk[2r], rk[2r+1] are the key words
+// of round r (k0 + r * 0x9E3779B9, k1 + r * 0xBB67AE85 mod 2^32).  When rk points into kernel
+// parameters the round keys are free operands; elsewhere they cost one load per round.
+__device__ __forceinline__ Ctr4 philox4x32_10_rk(Ctr4 c, const uint32_t *rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = Ctr4{hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0};
+    }
+    return c;
+}
+
 // Counter layout: (g, t, s | (draw-1) << 1 | (t >> 32) << 6, tag | (g >> 32) << 1).
 __device__ __forceinline__ Ctr4 draw_counter(uint64_t g, uint64_t t, int s, int draw, int tag)
 {
@@ -47,14 +63,15 @@ struct Rule {
     uint32_t np, nq;      // dyadic exponents
     uint32_t Pp, Pq;      // dyadic odd numerators (p = Pp / 2^np); 0/1 when n = 0
     uint64_t Tp, Tq;      // per-site thresholds floor(p * 2^32), floor(q * 2^32)
+    uint32_t rk[20];      // Philox round keys (see philox4x32_10_rk)
 };
 
 // xi words for V consecutive packed words starting at word unit u0 (= y * W + j) of
 // sublattice s at MCS t; dyadic construction of Sec. III: xi = r_n, then for i = n-1 .. 1
 // xi = b_i ? (r_i | xi) : (r_i & xi) where b_i is the i-th binary digit of the probability.
 template <int V>
-__device__ __forceinline__ void xi_dyadic(const Rule &R, uint64_t u0, uint64_t t, int s,
-                                          uint32_t (&xp)[V], uint32_t (&xq)[V])
+__device__ __forceinline__ void xi_dyadic(const Rule &R, const uint32_t *rk, uint64_t u0, uint64_t t,
+                                          int s, uint32_t (&xp)[V], uint32_t (&xq)[V])
 {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -64,13 +81,13 @@ __device__ __forceinline__ void xi_dyadic(const Rule &R, uint64_t u0, uint64_t t
     for (int i = (int)R.n_draws; i >= 1; --i) {
         uint32_t r[V];
         if (V == 4 && (u0 & 3) == 0) {
-            const Ctr4 o = philox4x32_10(draw_counter(u0 >> 2, t, s, i, 0), R.k0, R.k1);
+            const Ctr4 o = philox4x32_10_rk(draw_counter(u0 >> 2, t, s, i, 0), rk);
             r[0] = o.x; r[1 % V] = o.y; r[2 % V] = o.z; r[3 % V] = o.w;
         } else {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const uint64_t u = u0 + v;
-                r[v] = lane_of(philox4x32_10(draw_counter(u >> 2, t, s, i, 0), R.k0, R.k1),
+                r[v] = lane_of(philox4x32_10_rk(draw_counter(u >> 2, t, s, i, 0), rk),
                                (uint32_t)(u & 3));
             }
         }
@@ -91,18 +108,78 @@ __device__ __forceinline__ void xi_dyadic(const Rule &R, uint64_t u0, uint64_t t
     }
 }
 
+// The same construction with the number of draws ND known at compile time: all ND Philox
+// calls are independent, so they are issued first (the compiler interleaves their round
+// chains) and combined afterwards.  Requires R.n_draws == ND.
+template <int V, int ND>
+__device__ __forceinline__ void xi_dyadic_fixed(const Rule &R, const uint32_t *rk, uint64_t u0,
+                                                uint64_t t, int s, uint32_t (&xp)[V],
+                                                uint32_t (&xq)[V])
+{
+    uint32_t r[ND][V];
+    if (V == 4 && (u0 & 3) == 0) {
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+            const Ctr4 o = philox4x32_10_rk(draw_counter(u0 >> 2, t, s, i + 1, 0), rk);
+            r[i][0] = o.x; r[i][1 % V] = o.y; r[i][2 % V] = o.z; r[i][3 % V] = o.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < ND; ++i)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const uint64_t u = u0 + v;
+                r[i][v] = lane_of(philox4x32_10_rk(draw_counter(u >> 2, t, s, i + 1, 0), rk),
+                                  (uint32_t)(u & 3));
+            }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        xp[v] = (R.np == 0 && R.Pp) ? 0xFFFFFFFFu : 0u;
+        xq[v] = (R.nq == 0 && R.Pq) ? 0xFFFFFFFFu : 0u;
+    }
+#pragma unroll
+    for (int i = ND; i >= 1; --i) {
+        if (i <= (int)R.np) {
+            const bool first = (i == (int)R.np);
+            const bool bit = (R.Pp >> (R.np - i)) & 1u;
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                xp[v] = first ? r[i - 1][v] : (bit ? (r[i - 1][v] | xp[v]) : (r[i - 1][v] & xp[v]));
+        }
+        if (i <= (int)R.nq) {
+            const bool first = (i == (int)R.nq);
+            const bool bit = (R.Pq >> (R.nq - i)) & 1u;
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                xq[v] = first ? r[i - 1][v] : (bit ? (r[i - 1][v] | xq[v]) : (r[i - 1][v] & xq[v]));
+        }
+    }
+}
+
+// MODE 1 with ND draws: ND in 1..4 uses the fixed-count form, 0 the runtime loop.
+template <int V, int ND>
+__device__ __forceinline__ void xi_dyadic_any(const Rule &R, const uint32_t *rk, uint64_t u0,
+                                              uint64_t t, int s, uint32_t (&xp)[V],
+                                              uint32_t (&xq)[V])
+{
+    if constexpr (ND == 0) xi_dyadic<V>(R, rk, u0, t, s, xp, xq);
+    else xi_dyadic_fixed<V, ND>(R, rk, u0, t, s, xp, xq);
+}
+
 // xi words for one packed word from per-site uniforms (Sec. II.B: one random number per
 // site).  Site unit u = y * (L/2) + k, k = 32 * word + bit; four sites per Philox call.
 // Sites outside `need` are not drawn (their xi bits are irrelevant to the mask).
-__device__ __forceinline__ void xi_uniform_word(const Rule &R, uint64_t site0, uint64_t t, int s,
-                                                uint32_t need, uint32_t &xp, uint32_t &xq)
+__device__ __forceinline__ void xi_uniform_word(const Rule &R, const uint32_t *rk, uint64_t site0,
+                                                uint64_t t, int s, uint32_t need, uint32_t &xp,
+                                                uint32_t &xq)
 {
     xp = 0u;
     xq = 0u;
 #pragma unroll 2
     for (int g = 0; g < 8; ++g) {
         if (((need >> (4 * g)) & 0xFu) == 0u) continue;
-        const Ctr4 o = philox4x32_10(draw_counter((site0 >> 2) + g, t, s, 1, 1), R.k0, R.k1);
+        const Ctr4 o = philox4x32_10_rk(draw_counter((site0 >> 2) + g, t, s, 1, 1), rk);
         const uint32_t u[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
         for (int l = 0; l < 4; ++l) {

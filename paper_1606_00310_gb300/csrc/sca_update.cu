@@ -104,13 +104,13 @@ __global__ void __launch_bounds__(512) k_half_step(const HalfArgs a)
                     xiq[v] = a.R.Pq ? 0xFFFFFFFFu : 0u;
                 }
             } else if constexpr (MODE == 1) {
-                xi_dyadic<V>(a.R, row, a.t, s, xip, xiq);
+                xi_dyadic<V>(a.R, a.R.rk, row, a.t, s, xip, xiq);
             } else {
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const uint32_t need = eligible(xm[v], ym[v], xpl[v], ny[v]);
-                    xi_uniform_word(a.R, (uint64_t)y * (L / 2) + 32u * (j + v), a.t, s, need,
-                                    xip[v], xiq[v]);
+                    xi_uniform_word(a.R, a.R.rk, (uint64_t)y * (L / 2) + 32u * (j + v), a.t, s,
+                                    need, xip[v], xiq[v]);
                 }
             }
 #pragma unroll

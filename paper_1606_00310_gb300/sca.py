@@ -58,6 +58,7 @@ SIGNATURES = {
     "sca_batch_run": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.c_uint32, C.c_void_p,
                                 C.c_void_p]),
     "sca_batch_get_state": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t]),
+    "sca_batch_unit_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32]),
     "sca_batch_reset": (C.c_int, [C.c_void_p]),
     "sca_batch_time": (C.c_uint64, [C.c_void_p]),
     "sca_batch_free": (None, [C.c_void_p]),
@@ -323,6 +324,17 @@ class Batch:
         if want_obs:
             obs = [[Obs.from_c(out[i * n + k]) for k in range(n)] for i in range(self.count)]
         return obs, list(ens)
+
+    def unit_times(self):
+        """(start_ns, end_ns, first_lattice) per work unit of the last run."""
+        u = self.shape()["units"]
+        st = np.zeros(u, np.uint64)
+        en = np.zeros(u, np.uint64)
+        fl = np.zeros(u, np.int32)
+        check(load().sca_batch_unit_times(self._h, st.ctypes.data_as(C.c_void_p),
+                                          en.ctypes.data_as(C.c_void_p),
+                                          fl.ctypes.data_as(C.c_void_p), u), "sca_batch_unit_times")
+        return st, en, fl
 
     def get_state(self, index: int) -> np.ndarray:
         n = words_count(self.Ls[index])
