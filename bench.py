@@ -24,8 +24,12 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the serving run keeps one stream per active request; let up to 32 of them run concurrently
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "site updates/s"
 UNIT = "updates/s"
@@ -48,8 +52,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the p=1/2 context line")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble line")
-    ap.add_argument("--only", default="", choices=["", "batch"],
-                    help="run only the batched ensemble (sized by --batch-count/--batch-mcs)")
+    ap.add_argument("--only", default="", choices=["", "batch", "serve"],
+                    help="run only the batched ensemble (--batch-count/--batch-mcs) or the "
+                         "serving stream (--serve-requests)")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-slots", type=int, default=96)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving line")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-mcs", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -238,6 +246,49 @@ def run_batch_only(a):
     print(json.dumps({"metric": METRIC, "value": sites * a.batch_mcs / (ms / 1000.0), "unit": UNIT,
                       "workload": "batched ensemble, first %d lattices, %d MCS" % (len(ens), a.batch_mcs),
                       "ms": ms, "shape": shape, "ensemble_w2_final": w2[-1]}), flush=True)
+
+
+def run_serving(n_requests, slots):
+    """Serving: a Poisson stream (200 requests/s) of simulations with L log-uniform in
+    [256, 8192], p ~ U(0.5, 1), q = 1 - p (per-site uniforms), 512-8192 MCS, each observed at
+    1, 2, 4, ..., n; submitted at their arrival times to the library's continuous-batching
+    server under a 120 GB budget.  Latency = finish - arrival."""
+    import paper_1606_00310_gb300.sca as sca
+    from paper_1606_00310_gb300 import workloads
+    reqs = workloads.request_stream(n=n_requests)
+    with sca.Server(budget_bytes=120 * 10 ** 9, max_active=slots, max_L=8192) as srv:
+        warm = srv.submit(8192, 0.7, 0.3, 10 ** 6, 64)      # first-use set-up off the clock
+        srv.wait(warm)
+        srv.release(warm)
+        t_start = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            delay = t_start + r["arrival_s"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(r["L"], r["p"], r["q"], r["seed"], r["mcs"]))
+        infos = []
+        for tk in tickets:
+            rc, _, info = srv.wait(tk)
+            if rc != sca.OK:
+                raise RuntimeError("request %d failed: %d" % (tk, rc))
+            infos.append(info)
+        st = srv.stats()
+    lat = np.array([i.done_s - i.submit_s for i in infos])
+    queue = np.array([i.admit_s - i.submit_s for i in infos])
+    span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
+    updates = sum(r["L"] ** 2 * r["mcs"] for r in reqs)
+    offered = updates / max(reqs[-1]["arrival_s"], 1e-9)
+    return {"workload": "%d requests, Poisson 200/s, L log-uniform [256,8192] (x64), "
+                        "p~U(0.5,1), q=1-p (per-site uniform), MCS U[512,8192], 120 GB budget, "
+                        "%d slots" % (len(reqs), slots),
+            "value": updates / span, "unit": UNIT, "span_s": span,
+            "offered_updates_per_s": offered,
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "p50_queue_s": float(np.percentile(queue, 50)),
+            "p99_queue_s": float(np.percentile(queue, 99)),
+            "completed": int(st["completed"]), "max_bytes_budget": int(st["budget_bytes"])}
 
 
 def run_batched(sca, torch, stream, dev, L_single, peak):
@@ -454,6 +505,13 @@ def main():
         return
     if a.only == "batch":
         run_batch_only(a)
+        return
+    if a.only == "serve":
+        from paper_1606_00310_gb300 import build
+        build.build()
+        line = run_serving(a.serve_requests, a.serve_slots)
+        line["metric"] = METRIC
+        print(json.dumps(line), flush=True)
         return
     if world > 1:
         import torch

@@ -140,9 +140,11 @@ int sca_state_device(sca_sim *sim, uint32_t **words_dev);
 /* MCS completed so far. */
 uint64_t sca_time(const sca_sim *sim);
 
-/* Update kernel choice: 0 = automatic, 1 = two-pass (one launch per sublattice, paper
- * Fig. 3 structure), 2 = fused even+odd wavefront (one launch per MCS).  Results are
- * identical for every choice; only speed differs.  Errors: SCA_EINVAL. */
+/* Update kernel choice: 0 = automatic (fused when L is a multiple of 2048, L >= 32768 and the
+ * draws are not per-site uniforms, else two-pass), 1 = two-pass (one launch per sublattice, the
+ * paper's Fig. 3 structure), 2 = fused even+odd wavefront (one launch per MCS; needs L a
+ * multiple of 2048).  Results are identical for every choice; only speed differs.
+ * Errors: SCA_EINVAL. */
 int sca_set_kernel(sca_sim *sim, int kernel);
 
 /* Update kernel the simulation uses now (1 = two-pass, 2 = fused), after automatic choice. */
@@ -209,6 +211,71 @@ int sca_batch_get_state(sca_batch *b, uint32_t index, uint32_t *host_words, size
 int sca_batch_reset(sca_batch *b);
 uint64_t sca_batch_time(const sca_batch *b);
 void sca_batch_free(sca_batch *b);
+
+/* ---- serving: continuous batching of independent simulations -------------------------------
+ * A server owns a scheduler thread and up to max_active slots (a stream each).  Requests queue
+ * in arrival order and are admitted while a slot is free and the sum of admitted requests'
+ * state (sca_workspace_bytes(L) + 256 each) stays within budget_bytes; their memory comes from
+ * the device's stream-ordered pool.  Admitted requests run concurrently, each on its own
+ * stream, advancing in replayed CUDA graphs of 64 MCS; a request's results equal those of a
+ * sca_sim with the same parameters run alone.  Times are seconds since sca_server_create. */
+typedef struct sca_server sca_server;   /* opaque */
+
+typedef struct sca_request_info {
+    uint64_t ticket;
+    uint64_t n_mcs;
+    uint32_t n_obs;      /* observations the request returns */
+    int32_t status;      /* SCA_EBUSY while pending or running, then the final status */
+    uint32_t L;
+    uint32_t reserved;
+    double submit_s;     /* when submitted */
+    double admit_s;      /* when admitted to a slot (0: not yet) */
+    double done_s;       /* when finished (0: not yet) */
+} sca_request_info;
+
+typedef struct sca_server_stats {
+    uint64_t submitted, admitted, completed, cancelled, failed;
+    uint32_t active;        /* requests holding a slot now */
+    uint32_t pending;       /* requests waiting for a slot or memory */
+    uint64_t bytes_in_use;  /* state memory of admitted requests */
+    uint64_t budget_bytes;
+    uint64_t updates_done;  /* site updates of completed requests */
+} sca_server_stats;
+
+/* Create a server on the current device.  max_L bounds the lattice size of requests.  Errors:
+ * SCA_EINVAL, SCA_ECUDA. */
+int sca_server_create(size_t budget_bytes, uint32_t max_active, uint32_t max_L, sca_server **out);
+
+/* Queue one simulation: params (L, seed, p, q, rng), n_mcs steps from the flat state, observed
+ * at times[0..n_times-1] (increasing, within 1..n_mcs; n_mcs is appended if missing) or, if
+ * times is NULL, at 1, 2, 4, ... and n_mcs; at most 64 observations.  Returns at once with a
+ * ticket.  Errors: SCA_EINVAL (bad parameters, L above max_L), SCA_EBUDGET (the state alone
+ * exceeds the budget). */
+int sca_server_submit(sca_server *srv, const sca_params *params, uint64_t n_mcs,
+                      const uint64_t *times, uint32_t n_times, uint64_t *ticket);
+
+/* Result of a request without blocking: SCA_EBUSY while pending or running; otherwise its
+ * final status, with up to n_out observations copied to out (may be NULL) and info filled (may
+ * be NULL).  Errors: SCA_ENOTFOUND. */
+int sca_server_poll(sca_server *srv, uint64_t ticket, sca_obs *out, uint32_t n_out,
+                    sca_request_info *info);
+
+/* As sca_server_poll, but blocks until the request finishes or timeout_ms passes (negative:
+ * no limit); SCA_ETIMEOUT if it did not finish in time. */
+int sca_server_wait(sca_server *srv, uint64_t ticket, int timeout_ms, sca_obs *out,
+                    uint32_t n_out, sca_request_info *info);
+
+/* Cancel a pending or running request (its status becomes SCA_ECANCELED).  Finished requests
+ * are left as they are. */
+int sca_server_cancel(sca_server *srv, uint64_t ticket);
+
+/* Forget a finished request.  Errors: SCA_EBUSY (not finished), SCA_ENOTFOUND. */
+int sca_server_release(sca_server *srv, uint64_t ticket);
+
+int sca_server_get_stats(sca_server *srv, sca_server_stats *out);
+
+/* Stop the scheduler (running requests are cancelled) and free everything. */
+void sca_server_destroy(sca_server *srv);
 
 /* ---- observation without allocation ---------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot let the

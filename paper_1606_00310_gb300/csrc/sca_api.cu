@@ -79,10 +79,6 @@ int make_rule(const sca_params &prm, Rule &R)
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-struct Layout {
-    size_t state_bytes, off_b, off_h0, off_part, off_res, off_err, total;
-};
-constexpr int kResCap = 64;
 
 static bool layout_for(uint32_t L, Layout &lo)
 {
@@ -101,28 +97,6 @@ static bool layout_for(uint32_t L, Layout &lo)
 }  // namespace sca
 
 using namespace sca;
-
-struct sca_sim {
-    sca_params P;
-    Rule R;
-    uint32_t L, W;
-    Layout lo;
-    char *base;
-    bool own_mem;
-    uint32_t *buf[2];
-    int cur;
-    int64_t *h0;
-    ObsPartial *part;
-    ObsDev *res;
-    uint32_t *err;      // device word: bit 0 = a kernel wait gave up
-    cudaStream_t stream;
-    bool own_stream;
-    uint64_t t;
-    int kernel;
-    bool timing;
-    std::vector<cudaEvent_t> ev;      // start/stop pairs around update launches
-    uint64_t timed_launches;
-};
 
 static void finish_obs(sca_obs &o)
 {
@@ -155,7 +129,6 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
         if ((uintptr_t)dev_buf % 256 != 0) return fail(SCA_EINVAL, "device buffer not 256-byte aligned");
     }
     sca_sim *s = new sca_sim();
-    s->P = *params;
     s->R = R;
     s->L = params->L;
     s->W = params->L / 64;
@@ -230,12 +203,21 @@ int sca_set_kernel(sca_sim *s, int kernel)
     return SCA_OK;
 }
 
-static bool use_fused(const sca_sim *s)
+}  // extern "C"
+
+bool sca::use_fused(const sca_sim *s)
 {
     if (s->kernel == 1) return false;
     if (s->kernel == 2) return true;
-    return fused_supported(s->L);
+    // automatic: the fused kernel halves HBM traffic, which pays once the state is far larger
+    // than L2 and the update is not arithmetic-bound; smaller lattices and per-site uniform
+    // draws run faster with the two-pass kernel (more CTAs, no recomputed halo rows)
+    return fused_supported(s->L) && s->L >= 32768 && s->R.mode != 2;
 }
+
+extern "C" {
+
+}  // extern "C"
 
 static cudaError_t record_event(sca_sim *s)
 {
@@ -252,7 +234,7 @@ int sca_get_kernel(const sca_sim *s)
     return use_fused(s) ? 2 : 1;
 }
 
-static int step_impl(sca_sim *s, uint64_t n)
+int sca::step_impl(sca_sim *s, uint64_t n)
 {
     if (n == 0) return SCA_OK;
     const bool fused = use_fused(s);
@@ -284,6 +266,8 @@ static int step_impl(sca_sim *s, uint64_t n)
     }
     return SCA_OK;
 }
+
+extern "C" {
 
 static void clear_events(sca_sim *s)
 {

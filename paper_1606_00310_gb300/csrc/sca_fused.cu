@@ -95,7 +95,8 @@ struct FusedArgs {
     uint32_t L, W;
     int T;              // threads per CTA = W / V
     int nslabs;
-    uint64_t t;
+    uint64_t t;         // MCS index, or its offset from *t_dev when t_dev is set
+    const uint64_t *t_dev;
     Rule R;
     uint32_t *err;      // bit 0: a wait gave up
 };
@@ -193,6 +194,7 @@ __global__ void __launch_bounds__(512) k_fused_mcs(const FusedArgs a)
     const uint32_t W = a.W, L = a.L;
     const int T = a.T;
     const int lane = threadIdx.x;
+    const uint64_t tt = a.t_dev ? *a.t_dev + a.t : a.t;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint32_t *cE = reinterpret_cast<uint32_t *>(smem + 64);
     uint32_t *cO = cE + T;
@@ -243,13 +245,13 @@ __global__ void __launch_bounds__(512) k_fused_mcs(const FusedArgs a)
         const uint32_t y = gy(r);
         uint32_t *cur = slot(r), *nxt = slot(r + 1);
         half_row<V, MODE, ND>(cur, cur + W, cur + 2 * W, nxt + 3 * W, (y & 1u) != 0, lane, T, W, a.R,
-                          y, L, a.t, 0, cE);
+                          y, L, tt, 0, cE);
     };
     auto odd_row = [&](int r) {       // sublattice 1 at row r, reads rows r and r+1
         const uint32_t y = gy(r);
         uint32_t *cur = slot(r), *nxt = slot(r + 1);
         half_row<V, MODE, ND>(cur + 2 * W, cur + 3 * W, cur, nxt + W, (y & 1u) == 0, lane, T, W, a.R,
-                          y, L, a.t, 1, cO);
+                          y, L, tt, 1, cO);
     };
     auto prev_lane = [&]() { return lane == 0 ? T - 1 : lane - 1; };
 
@@ -330,12 +332,20 @@ template <int V, int MODE, int ND>
 static cudaError_t launch_fused_v(FusedArgs a, size_t smem, cudaStream_t st)
 {
     auto kern = k_fused_mcs<V, MODE, ND>;
+    // raise the shared-memory limit once, to what the largest lattice needs, so no later launch
+    // (including one being captured into a graph) has to change a kernel attribute
     static int configured_smem = 0;
-    if ((int)smem > configured_smem) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (configured_smem == 0) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        int want = (int)fused_smem_bytes(131072);
+        if (want > optin) want = optin;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e != cudaSuccess) return e;
-        configured_smem = (int)smem;
+        configured_smem = want;
     }
+    if ((int)smem > configured_smem) return cudaErrorInvalidConfiguration;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, a.T, smem);
     if (e != cudaSuccess) return e;
@@ -350,12 +360,12 @@ static cudaError_t launch_fused_v(FusedArgs a, size_t smem, cudaStream_t st)
 }
 
 cudaError_t launch_fused_mcs(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t,
-                             const Rule &R, uint32_t *err, cudaStream_t st)
+                             const Rule &R, uint32_t *err, cudaStream_t st, const uint64_t *t_dev)
 {
     if (!fused_supported(L)) return cudaErrorNotSupported;
     const uint32_t W = L / 64;
     const int V = fused_V(W);
-    FusedArgs a{src, dst, L, W, (int)(W / V), 0, t, R, err};
+    FusedArgs a{src, dst, L, W, (int)(W / V), 0, t, t_dev, R, err};
     const size_t smem = fused_smem_bytes(L);
     const int mode = (int)R.mode;
 #define SCA_FUSED_V(VV)                                                         \

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <string>
+#include <vector>
 
 #include "sca_rng.cuh"
 
@@ -36,11 +38,16 @@ struct ObsPartial {
 
 // Update kernels.  A is the canonical word array (in place for the two-pass path); src/dst
 // for the fused path.  Launch counts are added to the library's counter.
+// t_dev: when set, the MCS index is *t_dev + t, read by the kernel (lets a captured graph of
+// steps be replayed; launch_add_t / launch_set_t maintain the counter).
 cudaError_t launch_half_step(uint32_t *A, uint32_t L, uint64_t t, int s, const Rule &R,
-                             cudaStream_t st);
+                             cudaStream_t st, const uint64_t *t_dev = nullptr);
+cudaError_t launch_add_t(uint64_t *t_dev, uint64_t n, cudaStream_t st);
+cudaError_t launch_set_t(uint64_t *t_dev, uint64_t v, cudaStream_t st);
 // err: device word; bit 0 is set if a pipeline wait gave up (the result is then invalid).
 cudaError_t launch_fused_mcs(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t,
-                             const Rule &R, uint32_t *err, cudaStream_t st);
+                             const Rule &R, uint32_t *err, cudaStream_t st,
+                             const uint64_t *t_dev = nullptr);
 bool fused_supported(uint32_t L);
 size_t fused_smem_bytes(uint32_t L);
 
@@ -54,4 +61,43 @@ cudaError_t launch_observe(const uint32_t *A, uint32_t L, int64_t *h0, ObsPartia
 void count_launches(uint64_t n);
 int sm_count();
 
+// Workspace layout of one simulation (all offsets 256-byte aligned).
+struct Layout {
+    size_t state_bytes, off_b, off_h0, off_part, off_res, off_err, total;
+};
+constexpr int kResCap = 64;   // observation records per simulation
+
+}  // namespace sca
+
+struct sca_params;
+
+// One single-lattice simulation (opaque on the ABI).
+struct sca_sim {
+    sca::Rule R;
+    uint32_t L, W;
+    sca::Layout lo;
+    char *base;
+    bool own_mem;
+    uint32_t *buf[2];
+    int cur;
+    int64_t *h0;
+    sca::ObsPartial *part;
+    sca::ObsDev *res;
+    uint32_t *err;      // device word: bit 0 = a kernel wait gave up
+    cudaStream_t stream;
+    bool own_stream;
+    uint64_t t;
+    int kernel;
+    bool timing;
+    std::vector<cudaEvent_t> ev;      // start/stop pairs around update launches
+    uint64_t timed_launches;
+};
+
+
+namespace sca {
+int make_rule(const sca_params &prm, Rule &R);
+bool use_fused(const sca_sim *s);
+int step_impl(sca_sim *s, uint64_t n);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *where);
 }  // namespace sca

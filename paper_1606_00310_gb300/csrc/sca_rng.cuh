@@ -168,23 +168,34 @@ __device__ __forceinline__ void xi_dyadic_any(const Rule &R, const uint32_t *rk,
 }
 
 // xi words for one packed word from per-site uniforms (Sec. II.B: one random number per
-// site).  Site unit u = y * (L/2) + k, k = 32 * word + bit; four sites per Philox call.
-// Sites outside `need` are not drawn (their xi bits are irrelevant to the mask).
+// site).  Site unit u = y * (L/2) + k, k = 32 * word + bit; four sites per Philox call.  All
+// eight calls of a word are made (skipping ineligible groups would diverge within a warp and
+// save nothing); they run four at a time as independent chains.  Thresholds are 32-bit, with
+// p = 1 (threshold 2^32) carried by the all_p / all_q masks.
 __device__ __forceinline__ void xi_uniform_word(const Rule &R, const uint32_t *rk, uint64_t site0,
                                                 uint64_t t, int s, uint32_t need, uint32_t &xp,
                                                 uint32_t &xq)
 {
-    xp = 0u;
-    xq = 0u;
-#pragma unroll 2
-    for (int g = 0; g < 8; ++g) {
-        if (((need >> (4 * g)) & 0xFu) == 0u) continue;
-        const Ctr4 o = philox4x32_10_rk(draw_counter((site0 >> 2) + g, t, s, 1, 1), rk);
-        const uint32_t u[4] = {o.x, o.y, o.z, o.w};
+    (void)need;
+    const uint32_t Tp = R.Tp >= (1ull << 32) ? 0xFFFFFFFFu : (uint32_t)R.Tp;
+    const uint32_t Tq = R.Tq >= (1ull << 32) ? 0xFFFFFFFFu : (uint32_t)R.Tq;
+    const uint32_t all_p = R.Tp >= (1ull << 32) ? 0xFFFFFFFFu : 0u;
+    const uint32_t all_q = R.Tq >= (1ull << 32) ? 0xFFFFFFFFu : 0u;
+    xp = all_p;
+    xq = all_q;
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            xp |= (uint32_t)((uint64_t)u[l] < R.Tp) << (4 * g + l);
-            xq |= (uint32_t)((uint64_t)u[l] < R.Tq) << (4 * g + l);
+    for (int half = 0; half < 2; ++half) {
+        Ctr4 o[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            o[g] = philox4x32_10_rk(draw_counter((site0 >> 2) + 4 * half + g, t, s, 1, 1), rk);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int b = 16 * half + 4 * g;
+            xp |= ((uint32_t)(o[g].x < Tp) << b) | ((uint32_t)(o[g].y < Tp) << (b + 1)) |
+                  ((uint32_t)(o[g].z < Tp) << (b + 2)) | ((uint32_t)(o[g].w < Tp) << (b + 3));
+            xq |= ((uint32_t)(o[g].x < Tq) << b) | ((uint32_t)(o[g].y < Tq) << (b + 1)) |
+                  ((uint32_t)(o[g].z < Tq) << (b + 2)) | ((uint32_t)(o[g].w < Tq) << (b + 3));
         }
     }
 }

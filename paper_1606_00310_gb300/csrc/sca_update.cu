@@ -41,7 +41,8 @@ __device__ __forceinline__ void st_words(uint32_t *p, const uint32_t (&r)[V])
 struct HalfArgs {
     uint32_t *A;
     uint32_t L, W;
-    uint64_t t;
+    uint64_t t;          // MCS index, or its offset from *t_dev when t_dev is set
+    const uint64_t *t_dev;
     int s;
     int T;       // threads owning words in a team
     int TP;      // padded team size
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(512) k_half_step(const HalfArgs a)
     uint32_t *sh_carry = sh + tpb * a.TP + team * a.TP; // top mask bit of each lane
     const int s = a.s, ns = s ^ 1;
     const uint32_t L = a.L, W = a.W;
+    const uint64_t t = a.t_dev ? *a.t_dev + a.t : a.t;
     const size_t plane = (size_t)L * W;
     uint32_t *Asx = a.A + (size_t)(s * 2 + 0) * plane;
     uint32_t *Asy = a.A + (size_t)(s * 2 + 1) * plane;
@@ -104,12 +106,12 @@ __global__ void __launch_bounds__(512) k_half_step(const HalfArgs a)
                     xiq[v] = a.R.Pq ? 0xFFFFFFFFu : 0u;
                 }
             } else if constexpr (MODE == 1) {
-                xi_dyadic<V>(a.R, a.R.rk, row, a.t, s, xip, xiq);
+                xi_dyadic<V>(a.R, a.R.rk, row, t, s, xip, xiq);
             } else {
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const uint32_t need = eligible(xm[v], ym[v], xpl[v], ny[v]);
-                    xi_uniform_word(a.R, a.R.rk, (uint64_t)y * (L / 2) + 32u * (j + v), a.t, s,
+                    xi_uniform_word(a.R, a.R.rk, (uint64_t)y * (L / 2) + 32u * (j + v), t, s,
                                     need, xip[v], xiq[v]);
                 }
             }
@@ -191,11 +193,11 @@ static cudaError_t launch_half_v(const HalfArgs &a, const TeamShape &ts, cudaStr
 }
 
 cudaError_t launch_half_step(uint32_t *A, uint32_t L, uint64_t t, int s, const Rule &R,
-                             cudaStream_t st)
+                             cudaStream_t st, const uint64_t *t_dev)
 {
     const uint32_t W = L / 64;
     const TeamShape ts = team_shape(W, 256);
-    HalfArgs a{A, L, W, t, s, ts.T, ts.TP, R};
+    HalfArgs a{A, L, W, t, t_dev, s, ts.T, ts.TP, R};
     const int mode = (int)R.mode;
 #define SCA_HALF(VV)                                                        \
     if (ts.V == VV) {                                                       \
@@ -208,6 +210,28 @@ cudaError_t launch_half_step(uint32_t *A, uint32_t L, uint64_t t, int s, const R
     SCA_HALF(1)
 #undef SCA_HALF
     return cudaErrorInvalidValue;
+}
+
+}  // namespace sca
+
+namespace sca {
+
+// Advance a device-resident MCS counter (used by replayed step graphs).
+__global__ void k_add_t(uint64_t *t_dev, uint64_t n) { *t_dev += n; }
+__global__ void k_set_t(uint64_t *t_dev, uint64_t v) { *t_dev = v; }
+
+cudaError_t launch_add_t(uint64_t *t_dev, uint64_t n, cudaStream_t st)
+{
+    k_add_t<<<1, 1, 0, st>>>(t_dev, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_t(uint64_t *t_dev, uint64_t v, cudaStream_t st)
+{
+    k_set_t<<<1, 1, 0, st>>>(t_dev, v);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace sca

@@ -31,6 +31,19 @@ class sca_obs(C.Structure):
                 ("w2", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32)]
 
 
+class sca_request_info(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("n_mcs", C.c_uint64), ("n_obs", C.c_uint32),
+                ("status", C.c_int32), ("L", C.c_uint32), ("reserved", C.c_uint32),
+                ("submit_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double)]
+
+
+class sca_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
+                ("cancelled", C.c_uint64), ("failed", C.c_uint64), ("active", C.c_uint32),
+                ("pending", C.c_uint32), ("bytes_in_use", C.c_uint64),
+                ("budget_bytes", C.c_uint64), ("updates_done", C.c_uint64)]
+
+
 # Every symbol include/sca.h declares, with its ctypes signature.
 SIGNATURES = {
     "sca_workspace_bytes": (C.c_size_t, [C.c_uint32]),
@@ -62,6 +75,16 @@ SIGNATURES = {
     "sca_batch_reset": (C.c_int, [C.c_void_p]),
     "sca_batch_time": (C.c_uint64, [C.c_void_p]),
     "sca_batch_free": (None, [C.c_void_p]),
+    "sca_server_create": (C.c_int, [C.c_size_t, C.c_uint32, C.c_uint32, C.POINTER(C.c_void_p)]),
+    "sca_server_submit": (C.c_int, [C.c_void_p, C.POINTER(sca_params), C.c_uint64, C.c_void_p,
+                                    C.c_uint32, C.POINTER(C.c_uint64)]),
+    "sca_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32, C.c_void_p]),
+    "sca_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_uint32,
+                                  C.c_void_p]),
+    "sca_server_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "sca_server_release": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "sca_server_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sca_server_destroy": (None, [C.c_void_p]),
     "sca_observe_noalloc": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint64, C.c_void_p,
                                       C.POINTER(sca_obs)]),
     "sca_strerror": (C.c_char_p, [C.c_int]),
@@ -353,6 +376,73 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             load().sca_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching server (native scheduler thread inside the library)."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 64, max_L: int = 8192):
+        lib = load()
+        h = C.c_void_p()
+        check(lib.sca_server_create(int(budget_bytes), int(max_active), int(max_L), C.byref(h)),
+              "sca_server_create")
+        self._h = h
+
+    def submit(self, L, p, q, seed, n_mcs, times=None, rng=RNG_AUTO) -> int:
+        prm = sca_params(L=int(L), rng=int(rng), seed=int(seed), p=float(p), q=float(q))
+        tk = C.c_uint64()
+        if times:
+            arr = (C.c_uint64 * len(times))(*[int(x) for x in times])
+            rc = load().sca_server_submit(self._h, C.byref(prm), int(n_mcs), C.cast(arr, C.c_void_p),
+                                          len(times), C.byref(tk))
+        else:
+            rc = load().sca_server_submit(self._h, C.byref(prm), int(n_mcs), None, 0, C.byref(tk))
+        check(rc, "sca_server_submit")
+        return int(tk.value)
+
+    def _result(self, fn, ticket, *extra):
+        out = (sca_obs * 64)()
+        info = sca_request_info()
+        rc = fn(self._h, int(ticket), *extra, C.cast(out, C.c_void_p), 64, C.byref(info))
+        if rc in (ENOTFOUND, EINVAL):
+            raise ScaError(rc, "request %d" % ticket)
+        obs = [Obs.from_c(out[i]) for i in range(info.n_obs)] if rc in (OK, ESTATE) else None
+        return rc, obs, info
+
+    def poll(self, ticket):
+        """(status, observations or None, info)."""
+        return self._result(load().sca_server_poll, ticket)
+
+    def wait(self, ticket, timeout_ms: int = -1):
+        return self._result(load().sca_server_wait, ticket, int(timeout_ms))
+
+    def cancel(self, ticket):
+        check(load().sca_server_cancel(self._h, int(ticket)), "sca_server_cancel")
+
+    def release(self, ticket):
+        check(load().sca_server_release(self._h, int(ticket)), "sca_server_release")
+
+    def stats(self) -> dict:
+        st = sca_server_stats()
+        check(load().sca_server_get_stats(self._h, C.byref(st)), "sca_server_get_stats")
+        return {k: getattr(st, k) for k, _ in sca_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sca_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
