@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving line")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-mcs", type=int, default=4096)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -447,7 +447,7 @@ def run_ours(a, rank, world, local_rank):
 
     # context: the paper's own benchmark case p = 1/2, q = 0 (random bits every update)
     extra = None
-    if not a.no_extra and rank == 0 and (a.p, a.q) == (1.0, 0.0):
+    if not a.no_extra and rank == 0 and world == 1 and (a.p, a.q) == (1.0, 0.0):
         half = sca.Sim(L, seed=1, p=0.5, q=0.0, stream=stream, kernel=a.kernel)
         half.step(4)
         torch.cuda.synchronize(dev)
@@ -471,8 +471,11 @@ def run_ours(a, rank, world, local_rank):
                  "hbm_frac": BYTES_PER_UPDATE * L * L * n_half / (h_upd_ms / 1000.0) / 1e9 / peak}
 
     batched = None
-    if not a.no_batch and rank == 0 and (a.L, a.p, a.q) == (65536, 1.0, 0.0):
+    if not a.no_batch and rank == 0 and world == 1 and (a.L, a.p, a.q) == (65536, 1.0, 0.0):
         batched = run_batched(sca, torch, stream, dev, L, peak)
+    serving = None
+    if not a.no_serve and rank == 0 and world == 1 and (a.L, a.p, a.q) == (65536, 1.0, 0.0):
+        serving = run_serving(a.serve_requests, a.serve_slots)
 
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
@@ -491,6 +494,8 @@ def run_ours(a, rank, world, local_rank):
             line["context_p_half"] = extra
         if batched:
             line["batched"] = batched
+        if serving:
+            line["serving"] = serving
         print(json.dumps(line), flush=True)
     sim.close()
 
