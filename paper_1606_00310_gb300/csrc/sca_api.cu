@@ -135,6 +135,8 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
     s->lo = lo;
     s->t = 0;
     s->kernel = 0;
+    s->fused_V = 0;
+    s->fused_ring = 0;
     s->cur = 0;
     s->timing = false;
     s->timed_launches = 0;
@@ -228,6 +230,21 @@ static cudaError_t record_event(sca_sim *s)
     return cudaEventRecord(e, s->stream);
 }
 
+int sca_set_fused_shape(sca_sim *s, int words_per_thread, int ring)
+{
+    if (!s) return fail(SCA_EINVAL, "NULL simulation");
+    if (words_per_thread == 0) {
+        s->fused_V = 0;
+        s->fused_ring = 0;
+        return SCA_OK;
+    }
+    if (!fused_shape_ok(s->L, words_per_thread, ring))
+        return fail(SCA_EINVAL, "fused shape does not fit this lattice size");
+    s->fused_V = words_per_thread;
+    s->fused_ring = ring;
+    return SCA_OK;
+}
+
 int sca_get_kernel(const sca_sim *s)
 {
     if (!s) return fail(SCA_EINVAL, "NULL simulation");
@@ -247,7 +264,7 @@ int sca::step_impl(sca_sim *s, uint64_t n)
         cudaError_t e;
         if (fused) {
             e = launch_fused_mcs(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, t, s->R, s->err,
-                                 s->stream);
+                                 s->stream, nullptr, s->fused_V, s->fused_ring);
             if (e == cudaSuccess) s->cur ^= 1;
         } else {
             e = launch_half_step(s->buf[s->cur], s->L, t, 0, s->R, s->stream);

@@ -45,10 +45,12 @@ cudaError_t launch_half_step(uint32_t *A, uint32_t L, uint64_t t, int s, const R
 cudaError_t launch_add_t(uint64_t *t_dev, uint64_t n, cudaStream_t st);
 cudaError_t launch_set_t(uint64_t *t_dev, uint64_t v, cudaStream_t st);
 // err: device word; bit 0 is set if a pipeline wait gave up (the result is then invalid).
+// V_req / ring_req: launch shape (words per thread, row slots); 0 = default for L.
 cudaError_t launch_fused_mcs(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t,
                              const Rule &R, uint32_t *err, cudaStream_t st,
-                             const uint64_t *t_dev = nullptr);
+                             const uint64_t *t_dev = nullptr, int V_req = 0, int ring_req = 0);
 bool fused_supported(uint32_t L);
+bool fused_shape_ok(uint32_t L, int V, int ring);
 size_t fused_smem_bytes(uint32_t L);
 
 // Observation kernels: h0 scratch of L int64; partials scratch of obs_partials(L) + 1 entries
@@ -88,6 +90,7 @@ struct sca_sim {
     bool own_stream;
     uint64_t t;
     int kernel;
+    int fused_V, fused_ring;          // fused launch shape (0 = default)
     bool timing;
     std::vector<cudaEvent_t> ev;      // start/stop pairs around update launches
     uint64_t timed_launches;

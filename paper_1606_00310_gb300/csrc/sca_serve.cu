@@ -119,7 +119,8 @@ static cudaError_t capture_chunk(ServeReq *r, cudaStream_t st)
     cudaError_t le = cudaSuccess;
     for (uint32_t i = 0; i < kChunk && le == cudaSuccess; ++i) {
         if (fused) {
-            le = launch_fused_mcs(s->buf[cur], s->buf[cur ^ 1], s->L, i, s->R, s->err, st, r->t_dev);
+            le = launch_fused_mcs(s->buf[cur], s->buf[cur ^ 1], s->L, i, s->R, s->err, st, r->t_dev,
+                                  s->fused_V, s->fused_ring);
             cur ^= 1;
         } else {
             le = launch_half_step(s->buf[cur], s->L, i, 0, s->R, st, r->t_dev);

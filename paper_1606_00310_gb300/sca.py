@@ -59,6 +59,7 @@ SIGNATURES = {
     "sca_time": (C.c_uint64, [C.c_void_p]),
     "sca_set_kernel": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_get_kernel": (C.c_int, [C.c_void_p]),
+    "sca_set_fused_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "sca_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     "sca_free": (None, [C.c_void_p]),
@@ -208,6 +209,10 @@ class Sim:
 
     def set_kernel(self, kernel: int):
         check(load().sca_set_kernel(self._h, int(kernel)), "sca_set_kernel")
+
+    def set_fused_shape(self, words_per_thread: int, ring: int):
+        check(load().sca_set_fused_shape(self._h, int(words_per_thread), int(ring)),
+              "sca_set_fused_shape")
 
     def kernel_in_use(self) -> int:
         return int(load().sca_get_kernel(self._h))

@@ -264,3 +264,21 @@ def test_fused_against_oracle(sca):
     words_o, ora = oracle_run_obs(L, seed, p, q, times)
     assert_obs_equal(obs, ora)
     assert np.array_equal(words, words_o)
+
+
+@pytest.mark.parametrize("L,shape", [(8192, (4, 12)), (8192, (2, 8)), (16384, (2, 12)),
+                                     (4096, (1, 8)), (65536, (2, 12)), (65536, (4, 8))])
+def test_fused_launch_shapes_agree(sca, L, shape):
+    """Every launch shape of the fused kernel (words per thread, shared-memory ring depth)
+    gives the same state and sums as the two-pass kernel."""
+    times = [1, 2, 3]
+    res = []
+    for kernel, sh in ((sca.KERNEL_TWO_PASS, None), (sca.KERNEL_FUSED, shape)):
+        with sca.Sim(L, seed=17, p=0.75, q=0.25, kernel=kernel) as sim:
+            if sh:
+                sim.set_fused_shape(*sh)
+            obs = sim.run(times)
+            res.append(([(o.S1, o.S2, o.num) for o in obs], sim.state_tensor().clone()))
+    assert res[0][0] == res[1][0]
+    import torch
+    assert torch.equal(res[0][1], res[1][1])
