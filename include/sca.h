@@ -308,6 +308,12 @@ int sca_observe_noalloc(const uint32_t *words_dev, uint32_t L, uint64_t t, void 
 const char *sca_strerror(int status);
 const char *sca_last_error(void);   /* detail of the last failure on this thread */
 
+/* Failure-detection self-test: runs the bounded wait that every pipeline wait in the update
+ * kernels uses, on a barrier that nothing ever completes, with a limit of limit_us (1 us..2 s).
+ * Returns SCA_ETIMEOUT when the wait gave up and reported it, leaving the CUDA context usable;
+ * any other result means the timeout path is broken.  No trap, no fault, no unbounded spin. */
+int sca_selftest_wait_timeout(uint32_t limit_us);
+
 /* Number of kernels this library has launched in this process (all objects, all streams). */
 uint64_t sca_kernel_launches(void);
 

@@ -437,6 +437,29 @@ const char *sca_strerror(int status)
 
 const char *sca_last_error(void) { return g_last_error.c_str(); }
 
+int sca_selftest_wait_timeout(uint32_t limit_us)
+{
+    if (limit_us == 0 || limit_us > 2000000) return fail(SCA_EINVAL, "limit must be 1 us .. 2 s");
+    int dev = 0, khz = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    const long long cycles = (long long)limit_us * (khz > 0 ? khz : 2000000) / 1000;
+    uint32_t *err = nullptr;
+    cudaStream_t st = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocAsync(&err, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = launch_wait_selftest(cycles, err, st);
+    uint32_t h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (err) cudaFreeAsync(err, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+    return h ? fail(SCA_ETIMEOUT, "the wait gave up as designed") : SCA_OK;
+}
+
 uint64_t sca_kernel_launches(void) { return launches_total(); }
 
 }  // extern "C"

@@ -92,6 +92,43 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Wait until the mbarrier phase with `parity` completes, giving up after limit_cycles: then set
+// *abort (shared, so the rest of the CTA stops waiting at once) and bit 0 of *err (read by the
+// host) and return false.  Never traps and never spins without bound.
+__device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t parity, long long limit_cycles,
+                                             volatile int *abort, uint32_t *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long start = clock64();
+    while (!*abort) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - start > limit_cycles) {
+            *abort = 1;
+            atomicOr(err, 1u);
+        }
+    }
+    return false;
+}
+
+// Self-test of the wait limit: one thread waits on an mbarrier that nothing ever completes.
+__global__ void k_wait_selftest(long long limit_cycles, uint32_t *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ volatile int abort_flag;
+    if (threadIdx.x != 0) return;
+    abort_flag = 0;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    bounded_wait(&bar, 0u, limit_cycles, &abort_flag, err);
+}
+
+cudaError_t launch_wait_selftest(long long limit_cycles, uint32_t *err, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(limit_cycles, err);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 struct FusedArgs {
     const uint32_t *src;
     uint32_t *dst;
@@ -229,15 +266,7 @@ __global__ void __launch_bounds__(544) k_fused_mcs(const FusedArgs a)
     auto gy = [&](int r) -> uint32_t { return (uint32_t)(((int64_t)y0 - 2 + r + 2 * (int64_t)L) % L); };
     auto slot = [&](int r) -> uint32_t * { return ring + (size_t)(r % RING) * 4 * W; };
     auto wait_bar = [&](uint64_t *bar, uint32_t parity) {
-        if (mbar_try_wait(bar, parity)) return;
-        const long long start = clock64();
-        while (!abort_wait) {
-            if (mbar_try_wait(bar, parity)) return;
-            if (clock64() - start > kWaitCycles) {
-                abort_wait = 1;
-                atomicOr(a.err, 1u);
-            }
-        }
+        bounded_wait(bar, parity, kWaitCycles, &abort_wait, a.err);
     };
 
     if (lane == 0) {

@@ -50,6 +50,7 @@ cudaError_t launch_fused_mcs(const uint32_t *src, uint32_t *dst, uint32_t L, uin
                              const Rule &R, uint32_t *err, cudaStream_t st,
                              const uint64_t *t_dev = nullptr, int V_req = 0, int ring_req = 0);
 bool fused_supported(uint32_t L);
+cudaError_t launch_wait_selftest(long long limit_cycles, uint32_t *err, cudaStream_t st);
 bool fused_shape_ok(uint32_t L, int V, int ring);
 size_t fused_smem_bytes(uint32_t L);
 

@@ -91,6 +91,7 @@ SIGNATURES = {
     "sca_strerror": (C.c_char_p, [C.c_int]),
     "sca_last_error": (C.c_char_p, []),
     "sca_kernel_launches": (C.c_uint64, []),
+    "sca_selftest_wait_timeout": (C.c_int, [C.c_uint32]),
 }
 
 _lib = None

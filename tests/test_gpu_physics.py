@@ -1,0 +1,68 @@
+"""Physics and long-run checks on the GPU path at the sizes of the paper's workloads.
+
+* L = 4096, 10^4 MCS at 40 log-spaced times, dyadic (3/4, 1/4) and (1, 0), seeds 1-4: the exact
+  sums equal the oracle at every observation time the oracle reaches quickly (t <= 8), every
+  observation is valid (slopes close), and p = 1 follows its closed form to the end.
+* Growth exponent: q = 0 gives KPZ roughening with beta ~ 0.24 in 2+1 dimensions (paper
+  Sec. I.A cites the KPZ class; the value is from that literature).  At L = 4096 (saturation
+  time ~ L^1.6 >> 10^4) the fit W^2 = A t^(2 beta) + c over 16 <= t <= 10^4, averaged over
+  seeds, must give beta = 0.24 +- 0.01.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_1606_00310_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sca():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_00310_gb300 import build
+    build.build()
+    import paper_1606_00310_gb300.sca as mod
+    mod.load()
+    return mod
+
+
+@pytest.mark.parametrize("p,q", [(0.75, 0.25), (1.0, 0.0)])
+def test_mid_size_long_run_against_oracle_prefix(sca, p, q):
+    L = 4096
+    times = workloads.log_spaced_times(10_000, 40)
+    assert len(times) == 40 and times[-1] == 10_000
+    early = [t for t in times if t <= 8]
+    for seed in (1, 2, 3, 4):
+        with sca.Sim(L, seed=seed, p=p, q=q) as sim:
+            obs = sim.run(times)
+        assert all(x.status == 0 and x.num > 0 for x in obs)
+        if p == 1.0:
+            assert all(4 * x.num == x.N ** 2 for x in obs)
+        if seed in (1, 4):
+            bx, by = o.init_flat(L)
+            t = 0
+            for x in obs[:len(early)]:
+                o.run(bx, by, seed, p, q, t0=t, n_mcs=x.t - t)
+                t = x.t
+                r = o.observe(bx, by)
+                assert (x.S1, x.S2, x.num) == (r["S1"], r["S2"], r["num"]), (seed, x.t)
+
+
+def test_kpz_growth_exponent_large_lattice(sca):
+    optimize = pytest.importorskip("scipy.optimize")
+    L = 4096
+    times = workloads.log_times(8192) + [10_000]
+    w2 = np.zeros(len(times))
+    seeds = range(1, 5)
+    for seed in seeds:
+        with sca.Sim(L, seed=seed, p=0.5, q=0.0) as sim:
+            w2 += np.array([x.w2 for x in sim.run(times)])
+    w2 /= len(seeds)
+    t = np.array(times, float)
+    m = t >= 16
+    popt, _ = optimize.curve_fit(lambda t, A, b, c: A * t ** (2 * b) + c, t[m], w2[m],
+                                 p0=(0.3, 0.24, 0.3))
+    assert abs(popt[1] - 0.24) <= 0.01, popt
