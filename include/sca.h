@@ -184,15 +184,16 @@ typedef struct sca_batch sca_batch;   /* opaque */
  * Errors: SCA_EINVAL, SCA_ENOMEM, SCA_ECUDA. */
 int sca_batch_init(const sca_params *params, uint32_t count, void *stream, sca_batch **out);
 
-/* Launch shape: cluster size (1, 2, 4, 8 or 16 CTAs) and threads per CTA (128..512).  Every
- * shape gives identical results; sca_batch_tune picks the fastest.  Errors: SCA_EINVAL when a
- * lattice does not fit the cluster's shared memory. */
+/* Launch shape: cluster size (1..8 or 16 CTAs; a lattice may be split over any number of them,
+ * in parts that differ by at most one row) and threads per CTA (128..512).  Every shape gives
+ * identical results; sca_batch_tune picks the fastest.  Errors: SCA_EINVAL when a lattice does
+ * not fit the cluster's shared memory. */
 int sca_batch_set_shape(sca_batch *b, int cluster, int threads);
 int sca_batch_get_shape(const sca_batch *b, int *cluster, int *threads, int *clusters_launched,
                         int *units);
 
-/* Autotuner: times a probe_mcs-MCS run for each launch shape that fits (cluster sizes 4, 8, 16;
- * 256, 384, 512 threads), keeps the fastest, and leaves every lattice flat at MCS 0.  The
+/* Autotuner: times a probe_mcs-MCS run for each launch shape that fits (cluster sizes 4, 5, 6,
+ * 8, 16; 256, 384, 512 threads), keeps the fastest, and leaves every lattice flat at MCS 0.  The
  * chosen shape is returned through best_cluster / best_threads (either may be NULL).  Only
  * speed depends on the shape.  Errors: SCA_EINVAL, SCA_ECUDA. */
 int sca_batch_tune(sca_batch *b, uint32_t probe_mcs, int *best_cluster, int *best_threads);

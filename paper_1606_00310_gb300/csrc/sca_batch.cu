@@ -247,7 +247,7 @@ __device__ void batch_observe(cg::cluster_group &cluster, bool multi, uint32_t *
 {
     const uint32_t W = have ? lt.W : 1;
     const size_t P = (size_t)R * W;
-    const uint32_t r0 = (uint32_t)part * R;
+    const uint32_t r0 = have ? (uint32_t)((uint64_t)part * lt.L / lt.G) : 0;
     // column 0: site (0,y) is site 0 of sublattice y & 1; its sy- is bit 0 of word 0
     auto s0y = [&](uint32_t r) -> int64_t {
         const uint32_t y = r0 + r;
@@ -382,9 +382,10 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a)
         BatchLattice lt;
         if (have) lt = a.lat[slot.lattice];
         else { lt.L = 64; lt.W = 1; lt.G = 1; lt.V = 1; }
-        const uint32_t R = have ? lt.L / lt.G : 0;
+        // part p of a lattice split over G CTAs holds rows [p L / G, (p+1) L / G)
+        const uint32_t r0 = have ? (uint32_t)((uint64_t)slot.part * lt.L / lt.G) : 0;
+        const uint32_t R = have ? (uint32_t)((uint64_t)(slot.part + 1) * lt.L / lt.G) - r0 : 0;
         const uint32_t W = lt.W;
-        const uint32_t r0 = have ? (uint32_t)slot.part * R : 0;
         const int base_rank = rank - (have ? slot.part : 0);
         const size_t P = (size_t)R * W;
         const uint32_t items = have ? R * (W / lt.V) : 0;
@@ -393,9 +394,12 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a)
         // the sy- plane of the other sublattice, first row of the next part (periodic)
         uint32_t *remote_y[2] = {nullptr, nullptr};
         if (have) {
-            const int nrank = base_rank + (int)((slot.part + 1) % lt.G);
-            remote_y[0] = cluster.map_shared_rank(sm + (size_t)(1 * 2 + 1) * P, nrank);
-            remote_y[1] = cluster.map_shared_rank(sm + (size_t)(0 * 2 + 1) * P, nrank);
+            const uint32_t np = (slot.part + 1) % lt.G;
+            const int nrank = base_rank + (int)np;
+            const size_t Pn = (size_t)((uint32_t)((uint64_t)(np + 1) * lt.L / lt.G) -
+                                       (uint32_t)((uint64_t)np * lt.L / lt.G)) * W;   // its planes
+            remote_y[0] = cluster.map_shared_rank(sm + (size_t)(1 * 2 + 1) * Pn, nrank);
+            remote_y[1] = cluster.map_shared_rank(sm + (size_t)(0 * 2 + 1) * Pn, nrank);
             const uint32_t *g = a.state + lt.state_off;
             const size_t plane = (size_t)lt.L * W;
             for (uint32_t i = threadIdx.x; i < 4 * P; i += blockDim.x) {
@@ -486,7 +490,7 @@ struct BatchPlan {
 
 size_t batch_part_smem(uint32_t L, uint32_t G)
 {
-    const uint32_t W = L / 64, R = L / G;
+    const uint32_t W = L / 64, R = (L + G - 1) / G;      // the largest part
     const uint32_t V = (W % 4 == 0) ? 4 : (W % 2 == 0) ? 2 : 1;
     return 4 * (size_t)R * W * sizeof(uint32_t) + (size_t)R * sizeof(int32_t) +
            2 * (size_t)R * (W / V);
@@ -584,11 +588,17 @@ constexpr uint32_t kBatchMaxL = 2048;          // observation teams span at most
 constexpr int kBatchMaxObs = 64;
 constexpr size_t kBatchSmemCap = 200 * 1024;   // default shared memory per CTA for one part
 
+// Fewest CTAs whose shared memory holds the lattice (parts may differ by one row); among
+// those, prefer a count that divides the cluster so units have no idle CTAs.
 static uint32_t parts_needed(uint32_t L, int C, size_t cap)
 {
-    for (uint32_t G = 1; G <= (uint32_t)C; G <<= 1)
-        if (L % G == 0 && batch_part_smem(L, G) <= cap && (L / G) >= 2) return G;
-    return 0;
+    uint32_t g0 = 0;
+    for (uint32_t G = 1; G <= (uint32_t)C; ++G)
+        if (batch_part_smem(L, G) <= cap && (L / G) >= 2) { g0 = G; break; }
+    if (g0 == 0) return 0;
+    for (uint32_t G = g0; G <= (uint32_t)C; ++G)
+        if (C % G == 0) return G;
+    return g0;
 }
 }  // namespace sca
 
@@ -785,9 +795,9 @@ int sca_batch_init(const sca_params *params, uint32_t count, void *stream, sca_b
 int sca_batch_set_shape(sca_batch *b, int cluster, int threads)
 {
     if (!b) return fail(SCA_EINVAL, "NULL batch");
-    if (!(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16) ||
+    if (!((cluster >= 1 && cluster <= 8) || cluster == 16) ||
         !(threads == 128 || threads == 256 || threads == 384 || threads == 512))
-        return fail(SCA_EINVAL, "cluster must be 1, 2, 4, 8 or 16 and threads 128..512");
+        return fail(SCA_EINVAL, "cluster must be 1..8 or 16 and threads 128..512");
     return batch_plan(b, cluster, threads);
 }
 
@@ -915,8 +925,9 @@ int sca_batch_tune(sca_batch *b, uint32_t probe_mcs, int *best_cluster, int *bes
     struct Shape { int c, t; size_t cap; };
     // one CTA per SM with up to 200 KiB each, or two per SM with up to 100 KiB (more CTAs
     // per lattice, hence larger clusters)
-    const Shape shapes[] = {{8, 512, 200 * 1024}, {8, 384, 200 * 1024}, {8, 256, 200 * 1024},
-                            {16, 256, 100 * 1024}, {16, 512, 200 * 1024}, {4, 512, 200 * 1024}};
+    const Shape shapes[] = {{8, 512, 200 * 1024}, {6, 512, 200 * 1024}, {6, 384, 200 * 1024},
+                            {5, 512, 220 * 1024}, {8, 384, 200 * 1024}, {16, 256, 100 * 1024},
+                            {4, 512, 200 * 1024}};
     double best = 1e300;
     Shape bs{b->C, b->threads, b->cap};
     cudaEvent_t e0, e1;
