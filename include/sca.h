@@ -148,8 +148,8 @@ uint64_t sca_time(const sca_sim *sim);
 int sca_set_kernel(sca_sim *sim, int kernel);
 
 /* Launch shape of the fused kernel: words_per_thread (1, 2 or 4; the CTA has L/64 /
- * words_per_thread threads, 32..512) and ring = lattice rows held in shared memory (6, 8 or 12;
- * deeper rings prefetch further and leave stores more time).  0 restores the default (4 words,
+ * words_per_thread threads, 32..512) and ring = lattice rows held in shared memory (6; or 8 or
+ * 12 with 4 words per thread: deeper rings prefetch further and leave stores more time).  0 restores the default (4 words,
  * 6 rows).  Results do not depend
  * on the shape.  Errors: SCA_EINVAL if the shape does not fit L. */
 int sca_set_fused_shape(sca_sim *sim, int words_per_thread, int ring);

@@ -379,7 +379,8 @@ static bool shape_ok(uint32_t L, FusedShape sh)
 {
     if (L % 2048 != 0) return false;
     const uint32_t W = L / 64;
-    if (W % (uint32_t)sh.V != 0 || !(sh.ring == 6 || sh.ring == 8 || sh.ring == 12)) return false;
+    if (W % (uint32_t)sh.V != 0 || !(sh.ring == 6 || ((sh.ring == 8 || sh.ring == 12) && sh.V == 4)))
+        return false;
     const int T = (int)(W / sh.V);
     return T >= 32 && T <= 512 && T % 32 == 0;
 }
@@ -442,12 +443,12 @@ static cudaError_t launch_fused_r(FusedArgs a, size_t smem, cudaStream_t st)
 template <int V, int MODE, int ND>
 static cudaError_t launch_fused_v(FusedArgs a, size_t smem, cudaStream_t st)
 {
-    switch (a.ring) {
-    case 6: return launch_fused_r<V, MODE, ND, 6>(a, smem, st);
-    case 8: return launch_fused_r<V, MODE, ND, 8>(a, smem, st);
-    case 12: return launch_fused_r<V, MODE, ND, 12>(a, smem, st);
-    default: return cudaErrorInvalidValue;
+    if (a.ring == 6) return launch_fused_r<V, MODE, ND, 6>(a, smem, st);
+    if constexpr (V == 4) {            // deeper rings only with 4 words per thread
+        if (a.ring == 8) return launch_fused_r<V, MODE, ND, 8>(a, smem, st);
+        if (a.ring == 12) return launch_fused_r<V, MODE, ND, 12>(a, smem, st);
     }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fused_mcs(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t,

@@ -36,8 +36,18 @@ __global__ void __launch_bounds__(1024) k_obs_col0(const uint32_t *A, uint32_t L
         return 2 * (int64_t)(A[(size_t)(s * 2 + 1) * plane + (size_t)y * W] & 1u) - 1;
     };
     int64_t local = 0;
-    for (uint32_t y = y0; y < y0 + per && y < L; ++y)
-        if (y > 0) local += sy0(y);
+    // the rows of one thread are independent loads: issue them in batches so their latencies
+    // overlap instead of adding up
+    for (uint32_t yb = y0; yb < y0 + per && yb < L; yb += 8) {
+        int64_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t y = yb + k;
+            v[k] = (y < y0 + per && y < L && y > 0) ? sy0(y) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) local += v[k];
+    }
     int64_t incl = warp_incl_scan(local, 32);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 31) warp_tot[wid] = incl;
@@ -71,9 +81,28 @@ struct RowsArgs {
 // Rows: a team of threads spans row y; thread `lane` owns words j = lane*V .. lane*V+V-1 of
 // the even-x plane (sublattice y & 1) and the odd-x plane (sublattice (y & 1) ^ 1), i.e.
 // x in [64 j, 64 (j + V)).
+// Table over the 256 values of (4 even-x bits, 4 odd-x bits): for the 8 sites in x order
+// (e0, o0, e1, o1, ...), slopes s = 2b - 1, running offsets d_k = s_0 + ... + s_k:
+// bits 0-4: sum s + 8, bits 5-11: sum d + 36, bits 12-19: sum d^2.
+__device__ __forceinline__ uint32_t nibble_pair_entry(uint32_t i)
+{
+    int d = 0, sd = 0, sd2 = 0;
+    for (int k = 0; k < 4; ++k) {
+        d += 2 * (int)((i >> k) & 1u) - 1;
+        sd += d;
+        sd2 += d * d;
+        d += 2 * (int)((i >> (4 + k)) & 1u) - 1;
+        sd += d;
+        sd2 += d * d;
+    }
+    return (uint32_t)(d + 8) | ((uint32_t)(sd + 36) << 5) | ((uint32_t)sd2 << 12);
+}
+
 template <int V>
 __global__ void __launch_bounds__(1024) k_obs_rows(const RowsArgs a)
 {
+    __shared__ uint32_t tab[256];
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) tab[i] = nibble_pair_entry(i);
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t red1[32];
     __shared__ unsigned long long red2[32][2];
@@ -133,17 +162,20 @@ __global__ void __launch_bounds__(1024) k_obs_rows(const RowsArgs a)
             if (lane == 0 && total != 0) flags |= 2u;   // row does not close around x
             const int64_t s0 = 2 * (int64_t)(a.A[(size_t)((y & 1u) * 2) * plane + (size_t)y * W] & 1u) - 1;
             const int64_t H = a.h0[y] + excl - s0;      // h(x) = H + d(x), d summed from x0
+            // 8 sites at a time: with D the offset before a block and (S, A, B) its table entry,
+            // the block adds 8D + A to sum d, 8D^2 + 2DA + B to sum d^2, and S to D
             int32_t d = 0, sd = 0, sd2 = 0;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-#pragma unroll 8
-                for (int k = 0; k < 32; ++k) {
-                    d += 2 * (int32_t)((e[v] >> k) & 1u) - 1;
-                    sd += d;
-                    sd2 += d * d;
-                    d += 2 * (int32_t)((o[v] >> k) & 1u) - 1;
-                    sd += d;
-                    sd2 += d * d;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t ent = tab[((e[v] >> (4 * k)) & 0xFu) | (((o[v] >> (4 * k)) & 0xFu) << 4)];
+                    const int32_t S = (int32_t)(ent & 31u) - 8;
+                    const int32_t A = (int32_t)((ent >> 5) & 127u) - 36;
+                    const int32_t B = (int32_t)(ent >> 12);
+                    sd += 8 * d + A;
+                    sd2 += 8 * d * d + 2 * d * A + B;
+                    d += S;
                 }
             }
             const int64_t n = 64 * V;
@@ -180,17 +212,44 @@ __global__ void __launch_bounds__(1024) k_obs_rows(const RowsArgs a)
     }
 }
 
-__global__ void k_obs_final(const ObsPartial *part, int n, const ObsPartial *col_flag, uint32_t L,
-                            uint64_t t, ObsDev *out)
+__global__ void __launch_bounds__(256) k_obs_final(const ObsPartial *part, int n,
+                                                   const ObsPartial *col_flag, uint32_t L,
+                                                   uint64_t t, ObsDev *out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ long long s1w[8];
+    __shared__ unsigned long long s2w[8][2];
+    __shared__ uint32_t fw[8];
+    int64_t s1 = 0;
+    unsigned __int128 s2 = 0;
+    uint32_t flags = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        s1 += part[i].s1;
+        s2 += ((unsigned __int128)part[i].s2_hi << 64) | part[i].s2_lo;
+        flags |= part[i].flags;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_down_sync(0xFFFFFFFFu, s1, off);
+        const uint64_t lo = (uint64_t)s2, hi = (uint64_t)(s2 >> 64);
+        s2 += ((unsigned __int128)__shfl_down_sync(0xFFFFFFFFu, hi, off) << 64) |
+              __shfl_down_sync(0xFFFFFFFFu, lo, off);
+        flags |= __shfl_down_sync(0xFFFFFFFFu, flags, off);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s1w[w] = s1;
+        s2w[w][0] = (uint64_t)s2;
+        s2w[w][1] = (uint64_t)(s2 >> 64);
+        fw[w] = flags;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     __int128 S1 = 0;
     unsigned __int128 S2 = 0;
-    uint32_t flags = col_flag->flags;
-    for (int i = 0; i < n; ++i) {
-        S1 += part[i].s1;
-        S2 += ((unsigned __int128)part[i].s2_hi << 64) | part[i].s2_lo;
-        flags |= part[i].flags;
+    flags = col_flag->flags;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        S1 += s1w[k];
+        S2 += ((unsigned __int128)s2w[k][1] << 64) | s2w[k][0];
+        flags |= fw[k];
     }
     const unsigned __int128 N = (unsigned __int128)L * L;
     const unsigned __int128 num = N * S2 - (unsigned __int128)(S1 * S1);
@@ -226,7 +285,7 @@ cudaError_t launch_observe(const uint32_t *A, uint32_t L, int64_t *h0, ObsPartia
     if (ts.V == 4) k_obs_rows<4><<<grid, ts.block, 0, st>>>(ra);
     else if (ts.V == 2) k_obs_rows<2><<<grid, ts.block, 0, st>>>(ra);
     else k_obs_rows<1><<<grid, ts.block, 0, st>>>(ra);
-    k_obs_final<<<1, 32, 0, st>>>(partials, grid, col_flag, L, t, result);
+    k_obs_final<<<1, 256, 0, st>>>(partials, grid, col_flag, L, t, result);
     count_launches(3);
     return cudaGetLastError();
 }

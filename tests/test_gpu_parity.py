@@ -266,8 +266,8 @@ def test_fused_against_oracle(sca):
     assert np.array_equal(words, words_o)
 
 
-@pytest.mark.parametrize("L,shape", [(8192, (4, 12)), (8192, (2, 8)), (16384, (2, 12)),
-                                     (4096, (1, 8)), (65536, (2, 12)), (65536, (4, 8))])
+@pytest.mark.parametrize("L,shape", [(8192, (4, 12)), (8192, (4, 8)), (16384, (2, 6)),
+                                     (4096, (1, 6)), (65536, (2, 6)), (65536, (4, 8))])
 def test_fused_launch_shapes_agree(sca, L, shape):
     """Every launch shape of the fused kernel (words per thread, shared-memory ring depth)
     gives the same state and sums as the two-pass kernel."""

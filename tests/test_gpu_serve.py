@@ -127,3 +127,29 @@ def test_cancel_timeout_and_bad_requests(sca):
             assert e.value.code == sca.EINVAL
         st = srv.stats()
         assert st["cancelled"] >= 5 and st["failed"] == 0
+
+
+def test_request_stream_sample_against_oracle(sca):
+    """Requests drawn from the serving workload (non-dyadic p, q = 1 - p, 512-8192 MCS): the
+    small ones, served while larger ones from the same stream run beside them, equal the
+    oracle at every observation time."""
+    from paper_1606_00310_gb300 import workloads
+    stream = workloads.request_stream(n=2000)
+    small = [r for r in stream if r["L"] <= 384 and r["mcs"] <= 2000][:3]
+    big = [r for r in stream if r["L"] >= 2048][:4]
+    assert len(small) == 3
+    with sca.Server(budget_bytes=16 << 30, max_active=8, max_L=8192) as srv:
+        tk_big = [srv.submit(r["L"], r["p"], r["q"], r["seed"], r["mcs"]) for r in big]
+        tk_small = [srv.submit(r["L"], r["p"], r["q"], r["seed"], r["mcs"]) for r in small]
+        results = [srv.wait(tk, 300000) for tk in tk_small]
+        for tk in tk_big:
+            srv.cancel(tk)
+    for r, (rc, obs, _) in zip(small, results):
+        assert rc == sca.OK
+        bx, by = o.init_flat(r["L"])
+        t = 0
+        for x in obs:
+            o.run(bx, by, r["seed"], r["p"], r["q"], mode=o.UNIFORM32, t0=t, n_mcs=x.t - t)
+            t = x.t
+            ref = o.observe(bx, by)
+            assert (x.S1, x.S2, x.num) == (ref["S1"], ref["S2"], ref["num"]), (r, x.t)
