@@ -141,11 +141,18 @@ int sca_state_device(sca_sim *sim, uint32_t **words_dev);
 uint64_t sca_time(const sca_sim *sim);
 
 /* Update kernel choice: 0 = automatic (fused when L is a multiple of 2048, L >= 32768 and the
- * draws are not per-site uniforms, else two-pass), 1 = two-pass (one launch per sublattice, the
+ * draws are not per-site uniforms; temporal blocking for dyadic draws up to L = 8192 and for
+ * per-site uniforms up to L = 2048; else two-pass), 1 = two-pass (one launch per sublattice, the
  * paper's Fig. 3 structure), 2 = fused even+odd wavefront (one launch per MCS; needs L a
- * multiple of 2048).  Results are identical for every choice; only speed differs.
+ * multiple of 2048), 3 = temporal blocking (several MCS per launch in shared memory, see
+ * sca_set_temporal_block).  Results are identical for every choice; only speed differs.
  * Errors: SCA_EINVAL. */
 int sca_set_kernel(sca_sim *sim, int kernel);
+
+/* Temporal blocking (kernel 3 of sca_set_kernel): each launch advances mcs_per_launch MCS
+ * (a divisor of 64; 0 = default 4) with every CTA's rows and a halo of 2 rows per MCS held in
+ * shared memory.  Errors: SCA_EINVAL if the slab with its halo does not fit for this L. */
+int sca_set_temporal_block(sca_sim *sim, int mcs_per_launch);
 
 /* Launch shape of the fused kernel: words_per_thread (1, 2 or 4; the CTA has L/64 /
  * words_per_thread threads, 32..512) and ring = lattice rows held in shared memory (6; or 8 or
@@ -154,7 +161,8 @@ int sca_set_kernel(sca_sim *sim, int kernel);
  * on the shape.  Errors: SCA_EINVAL if the shape does not fit L. */
 int sca_set_fused_shape(sca_sim *sim, int words_per_thread, int ring);
 
-/* Update kernel the simulation uses now (1 = two-pass, 2 = fused), after automatic choice. */
+/* Update kernel the simulation uses now (1 = two-pass, 2 = fused, 3 = temporal blocking), after
+ * automatic choice. */
 int sca_get_kernel(const sca_sim *sim);
 
 /* Kernel timing: while enabled, the library records a CUDA event pair on the simulation's

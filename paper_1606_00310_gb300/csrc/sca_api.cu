@@ -137,6 +137,8 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
     s->kernel = 0;
     s->fused_V = 0;
     s->fused_ring = 0;
+    s->tb_k = 4;
+    s->tb_set = false;
     s->cur = 0;
     s->timing = false;
     s->timed_launches = 0;
@@ -198,24 +200,64 @@ int sca_reset(sca_sim *s)
 
 int sca_set_kernel(sca_sim *s, int kernel)
 {
-    if (!s || kernel < 0 || kernel > 2) return fail(SCA_EINVAL, "kernel must be 0, 1 or 2");
+    if (!s || kernel < 0 || kernel > 3) return fail(SCA_EINVAL, "kernel must be 0, 1, 2 or 3");
     if (kernel == 2 && !fused_supported(s->L))
-        return fail(SCA_EINVAL, "fused kernel needs L to be a multiple of 256");
+        return fail(SCA_EINVAL, "fused kernel needs L to be a multiple of 2048");
+    if (kernel == 3) {
+        uint32_t ns;
+        size_t sm;
+        if (!tblock_plan(s->L, (uint32_t)s->tb_k, &ns, &sm))
+            return fail(SCA_EINVAL, "temporal blocking does not fit this lattice size");
+    }
     s->kernel = kernel;
+    return SCA_OK;
+}
+
+int sca_set_temporal_block(sca_sim *s, int mcs_per_launch)
+{
+    if (!s) return fail(SCA_EINVAL, "NULL simulation");
+    const int k = mcs_per_launch > 0 ? mcs_per_launch : 4;
+    if (k > 64 || (64 % k) != 0) return fail(SCA_EINVAL, "MCS per launch must divide 64");
+    uint32_t ns;
+    size_t sm;
+    if (!tblock_plan(s->L, (uint32_t)k, &ns, &sm))
+        return fail(SCA_EINVAL, "temporal blocking does not fit this lattice size");
+    s->tb_k = k;
+    s->tb_set = true;
     return SCA_OK;
 }
 
 }  // extern "C"
 
-bool sca::use_fused(const sca_sim *s)
+// Automatic kernel choice (measured on GB300): the fused kernel halves HBM traffic, which pays
+// once the state is far larger than L2 and the update is not arithmetic-bound; temporal
+// blocking (several MCS per launch in shared memory) wins while the lattice is small enough
+// that launches and L2 round trips dominate (dyadic draws up to L = 8192, per-site uniforms up
+// to L = 2048); the two-pass kernel covers the rest.
+int sca::effective_kernel(const sca_sim *s, int *tb_k)
 {
-    if (s->kernel == 1) return false;
-    if (s->kernel == 2) return true;
-    // automatic: the fused kernel halves HBM traffic, which pays once the state is far larger
-    // than L2 and the update is not arithmetic-bound; smaller lattices and per-site uniform
-    // draws run faster with the two-pass kernel (more CTAs, no recomputed halo rows)
-    return fused_supported(s->L) && s->L >= 32768 && s->R.mode != 2;
+    int k = s->kernel;
+    int kk = s->tb_k;
+    if (k == 0) {
+        uint32_t ns;
+        size_t sm;
+        if (fused_supported(s->L) && s->L >= 32768 && s->R.mode != 2) {
+            k = 2;
+        } else if (s->R.mode != 2 && s->L <= 8192 && tblock_plan(s->L, s->tb_set ? kk : 8, &ns, &sm)) {
+            k = 3;
+            if (!s->tb_set) kk = 8;
+        } else if (s->R.mode == 2 && s->L <= 2048 && tblock_plan(s->L, s->tb_set ? kk : 4, &ns, &sm)) {
+            k = 3;
+            if (!s->tb_set) kk = 4;
+        } else {
+            k = 1;
+        }
+    }
+    if (tb_k) *tb_k = kk;
+    return k;
 }
+
+bool sca::use_fused(const sca_sim *s) { return effective_kernel(s, nullptr) == 2; }
 
 extern "C" {
 
@@ -248,13 +290,41 @@ int sca_set_fused_shape(sca_sim *s, int words_per_thread, int ring)
 int sca_get_kernel(const sca_sim *s)
 {
     if (!s) return fail(SCA_EINVAL, "NULL simulation");
-    return use_fused(s) ? 2 : 1;
+    return effective_kernel(s, nullptr);
 }
 
 int sca::step_impl(sca_sim *s, uint64_t n)
 {
     if (n == 0) return SCA_OK;
-    const bool fused = use_fused(s);
+    int tbk = 0;
+    const int kern = effective_kernel(s, &tbk);
+    const bool fused = kern == 2;
+    if (kern == 3) {                           // temporal blocking: tbk MCS per launch
+        if (s->timing) {
+            cudaError_t e = record_event(s);
+            if (e != cudaSuccess) return cuda_fail(e, "timing event");
+        }
+        uint64_t done = 0, launches = 0;
+        while (done < n) {
+            const uint64_t k = (n - done) < (uint64_t)tbk ? (n - done) : (uint64_t)tbk;
+            cudaError_t e = launch_tblock(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->t + done,
+                                          (uint32_t)k, s->R, s->stream);
+            if (e != cudaSuccess) {
+                s->t += done;
+                return cuda_fail(e, "temporal-blocking launch");
+            }
+            s->cur ^= 1;
+            done += k;
+            ++launches;
+        }
+        s->t += n;
+        if (s->timing) {
+            s->timed_launches += launches;
+            cudaError_t e = record_event(s);
+            if (e != cudaSuccess) return cuda_fail(e, "timing event");
+        }
+        return SCA_OK;
+    }
     if (s->timing) {
         cudaError_t e = record_event(s);
         if (e != cudaSuccess) return cuda_fail(e, "timing event");

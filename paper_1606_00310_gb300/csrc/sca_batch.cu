@@ -148,12 +148,15 @@ __device__ __forceinline__ void batch_item(uint32_t *own_x, uint32_t *own_y, uin
 // Carries live in two byte arrays, one byte per item (row-major, W / V items per row): the
 // half-step of sublattice s reads the carries pending for its own sx- words from cbuf[s] and
 // writes the ones it produces into cbuf[s ^ 1], so reads and writes never meet.
+// Update rows 0..R-1 of the CTA's rows held in shared memory (planes of plane_rows rows each);
+// row r is lattice row (r0 + r) mod L; the row after the last updated row is remote_nb_y.
 template <int V, int MODE, int ND>
 __device__ void batch_half_step(uint32_t *sm, uint8_t *cbuf, const BatchLattice &lt, const uint32_t *rk,
-                                uint32_t R, uint32_t r0, uint32_t *remote_nb_y, int s, uint64_t t)
+                                uint32_t R, uint32_t r0, uint32_t *remote_nb_y, int s, uint64_t t,
+                                uint32_t plane_rows)
 {
     const uint32_t W = lt.W;
-    const size_t P = (size_t)R * W;
+    const size_t P = (size_t)plane_rows * W;
     uint32_t *own_x = sm + (size_t)(s * 2 + 0) * P;
     uint32_t *own_y = sm + (size_t)(s * 2 + 1) * P;
     uint32_t *nbx = sm + (size_t)((s ^ 1) * 2 + 0) * P;
@@ -167,7 +170,7 @@ __device__ void batch_half_step(uint32_t *sm, uint8_t *cbuf, const BatchLattice 
     for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
         const uint32_t r = pow2 ? it >> sh : it / per_row;
         const uint32_t q = it - r * per_row;
-        const uint32_t y = r0 + r;
+        const uint32_t y = (r0 + r < lt.L) ? r0 + r : r0 + r - lt.L;
         uint32_t *nyn = (r + 1 < R) ? nby + (size_t)(r + 1) * W : remote_nb_y;
         batch_item<V, MODE, ND>(own_x + (size_t)r * W, own_y + (size_t)r * W, nbx + (size_t)r * W, nyn,
                             q * V, W, ((uint32_t)s + y) & 1u, lt.R, rk, y, lt.L, t, s, c_rd[it],
@@ -177,18 +180,19 @@ __device__ void batch_half_step(uint32_t *sm, uint8_t *cbuf, const BatchLattice 
 
 template <int V>
 __device__ void batch_half_step_v(uint32_t *sm, uint8_t *cbuf, const BatchLattice &lt, const uint32_t *rk,
-                                  uint32_t R, uint32_t r0, uint32_t *remote_nb_y, int s, uint64_t t)
+                                  uint32_t R, uint32_t r0, uint32_t *remote_nb_y, int s, uint64_t t,
+                                  uint32_t plane_rows)
 {
-    if (lt.R.mode == 0) batch_half_step<V, 0, 0>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t);
+    if (lt.R.mode == 0) batch_half_step<V, 0, 0>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t, plane_rows);
     else if (lt.R.mode == 1) {
         switch (lt.R.n_draws) {
-        case 1: batch_half_step<V, 1, 1>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t); break;
-        case 2: batch_half_step<V, 1, 2>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t); break;
-        case 3: batch_half_step<V, 1, 3>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t); break;
-        case 4: batch_half_step<V, 1, 4>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t); break;
-        default: batch_half_step<V, 1, 0>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t); break;
+        case 1: batch_half_step<V, 1, 1>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t, plane_rows); break;
+        case 2: batch_half_step<V, 1, 2>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t, plane_rows); break;
+        case 3: batch_half_step<V, 1, 3>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t, plane_rows); break;
+        case 4: batch_half_step<V, 1, 4>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t, plane_rows); break;
+        default: batch_half_step<V, 1, 0>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t, plane_rows); break;
         }
-    } else batch_half_step<V, 2, 0>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t);
+    } else batch_half_step<V, 2, 0>(sm, cbuf, lt, rk, R, r0, remote_nb_y, s, t, plane_rows);
 }
 
 // Apply the carries pending after an odd half-step (they belong to sublattice 0's sx- words,
@@ -416,9 +420,9 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a)
         for (uint64_t t = a.t0; t < t_end; ++t) {
             for (int s = 0; s < 2; ++s) {
                 if (have) {
-                    if (lt.V == 4) batch_half_step_v<4>(sm, cbuf, lt, s_rk, R, r0, remote_y[s], s, t);
-                    else if (lt.V == 2) batch_half_step_v<2>(sm, cbuf, lt, s_rk, R, r0, remote_y[s], s, t);
-                    else batch_half_step_v<1>(sm, cbuf, lt, s_rk, R, r0, remote_y[s], s, t);
+                    if (lt.V == 4) batch_half_step_v<4>(sm, cbuf, lt, s_rk, R, r0, remote_y[s], s, t, R);
+                    else if (lt.V == 2) batch_half_step_v<2>(sm, cbuf, lt, s_rk, R, r0, remote_y[s], s, t, R);
+                    else batch_half_step_v<1>(sm, cbuf, lt, s_rk, R, r0, remote_y[s], s, t, R);
                 }
                 if (multi) cluster.sync();
                 else __syncthreads();
@@ -479,6 +483,128 @@ __global__ void k_batch_finalize(const BatchLattice *lat, int n_lat, const ObsPa
     o.status = flags ? -7 : 0;
     o.reserved = (int32_t)flags;
     out[i] = o;
+}
+
+// ------------------------------------------------------------- single lattice, k MCS per pass
+// Temporal blocking (multi-MCS per launch) for lattices whose state is too small to keep HBM
+// busy but too large for one cluster's shared memory.  CTA b owns rows [y0, y1) and loads them
+// with a halo of 2k rows on each side into shared memory; it then runs k MCS there (each
+// half-step leaves one more row at each end of the loaded block stale, since an update at row
+// r reads and writes rows r and r+1), so after k MCS exactly rows [y0, y1) are current and are
+// written to the other state buffer.  The halo updates are recomputed by the neighbouring
+// CTAs with the same counter-based random numbers.  Half-steps reuse the batch kernel's
+// shared-memory update.
+struct TBArgs {
+    const uint32_t *src;
+    uint32_t *dst;
+    uint32_t L, W, V, k, nslabs;
+    uint64_t t0;             // MCS index of the first step, or offset from *t_dev
+    const uint64_t *t_dev;
+    Rule R;
+};
+
+__global__ void __launch_bounds__(512, 1) k_tblock(const TBArgs a)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ uint32_t s_rk[20];
+    const uint32_t L = a.L, W = a.W, k = a.k;
+    const uint32_t b = blockIdx.x;
+    const uint32_t y0 = (uint32_t)((uint64_t)b * L / a.nslabs);
+    const uint32_t y1 = (uint32_t)((uint64_t)(b + 1) * L / a.nslabs);
+    const uint32_t n = y1 - y0, N = n + 4 * k;
+    const uint32_t first = (y0 + L - 2 * k) % L;
+    const size_t P = (size_t)N * W, plane = (size_t)L * W;
+    const uint32_t items = (N - 1) * (W / a.V);
+    uint8_t *cbuf = reinterpret_cast<uint8_t *>(sm + 4 * P);
+    for (size_t i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+        const uint32_t pl = (uint32_t)(i / P);
+        const size_t rem = i - (size_t)pl * P;
+        const uint32_t r = (uint32_t)(rem / W), j = (uint32_t)(rem - (size_t)r * W);
+        uint32_t y = first + r;
+        if (y >= L) y -= L;
+        sm[i] = a.src[(size_t)pl * plane + (size_t)y * W + j];
+    }
+    for (uint32_t i = threadIdx.x; i < 2 * items; i += blockDim.x) cbuf[i] = 0;
+    if (threadIdx.x < 20) s_rk[threadIdx.x] = a.R.rk[threadIdx.x];
+    BatchLattice lt;
+    lt.L = L;
+    lt.W = W;
+    lt.V = a.V;
+    lt.G = 1;
+    lt.R = a.R;
+    const uint64_t t0 = a.t_dev ? *a.t_dev + a.t0 : a.t0;
+    __syncthreads();
+    for (uint32_t m = 0; m < k; ++m) {
+        for (int s = 0; s < 2; ++s) {
+            // rows 0..N-2 are updated; row N-1 only supplies sy+ for row N-2
+            uint32_t *last_y = sm + (size_t)((s ^ 1) * 2 + 1) * P + (size_t)(N - 1) * W;
+            if (a.V == 4) batch_half_step_v<4>(sm, cbuf, lt, s_rk, N - 1, first, last_y, s, t0 + m, N);
+            else if (a.V == 2) batch_half_step_v<2>(sm, cbuf, lt, s_rk, N - 1, first, last_y, s, t0 + m, N);
+            else batch_half_step_v<1>(sm, cbuf, lt, s_rk, N - 1, first, last_y, s, t0 + m, N);
+            __syncthreads();
+        }
+    }
+    batch_flush_carry(sm, cbuf, lt, N - 1);
+    __syncthreads();
+    const size_t PN = (size_t)n * W;
+    for (size_t i = threadIdx.x; i < 4 * PN; i += blockDim.x) {
+        const uint32_t pl = (uint32_t)(i / PN);
+        const size_t rem = i - (size_t)pl * PN;
+        const uint32_t r = (uint32_t)(rem / W), j = (uint32_t)(rem - (size_t)r * W);
+        a.dst[(size_t)pl * plane + (size_t)(y0 + r) * W + j] = sm[(size_t)pl * P + (size_t)(r + 2 * k) * W + j];
+    }
+}
+
+size_t tblock_smem(uint32_t L, uint32_t n, uint32_t k)
+{
+    const uint32_t W = L / 64, V = (W % 4 == 0) ? 4 : (W % 2 == 0) ? 2 : 1, N = n + 4 * k;
+    return 4 * (size_t)N * W * sizeof(uint32_t) + 2 * (size_t)(N - 1) * (W / V);
+}
+
+// Slab count: at least one CTA per SM, and slabs of at least 4k rows so the recomputed halo
+// stays at most half of the work; shared memory must hold a slab with its halo.
+bool tblock_plan(uint32_t L, uint32_t k, uint32_t *nslabs, size_t *smem)
+{
+    if (L < 128 || L % 64 != 0 || k == 0 || 4 * k >= L) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t cap = (size_t)optin - 1024;
+    uint32_t ns = (uint32_t)sm_count();
+    if (ns > L / (4 * k)) ns = L / (4 * k);
+    if (ns == 0) ns = 1;
+    while (tblock_smem(L, (L + ns - 1) / ns, k) > cap && ns < L / 2) ns *= 2;
+    if (tblock_smem(L, (L + ns - 1) / ns, k) > cap) return false;
+    *nslabs = ns;
+    *smem = tblock_smem(L, (L + ns - 1) / ns, k);
+    return true;
+}
+
+cudaError_t launch_tblock(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t0, uint32_t k,
+                          const Rule &R, cudaStream_t st, const uint64_t *t_dev)
+{
+    uint32_t ns = 0;
+    size_t smem = 0;
+    if (!tblock_plan(L, k, &ns, &smem)) return cudaErrorInvalidValue;
+    static int configured = 0;
+    if (!configured) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_tblock);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_tblock, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+        configured = optin - (int)fa.sharedSizeBytes;
+    }
+    if ((int)smem > configured) return cudaErrorInvalidConfiguration;
+    const uint32_t W = L / 64;
+    TBArgs a{src, dst, L, W, (W % 4 == 0) ? 4u : (W % 2 == 0) ? 2u : 1u, k, ns, t0, t_dev, R};
+    k_tblock<<<ns, 512, smem, st>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------- host

@@ -51,6 +51,10 @@ cudaError_t launch_fused_mcs(const uint32_t *src, uint32_t *dst, uint32_t L, uin
                              const uint64_t *t_dev = nullptr, int V_req = 0, int ring_req = 0);
 bool fused_supported(uint32_t L);
 cudaError_t launch_wait_selftest(long long limit_cycles, uint32_t *err, cudaStream_t st);
+// Temporal blocking: k MCS per launch, src -> dst (ping-pong), MCS index t0 (+ *t_dev if set).
+cudaError_t launch_tblock(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t0, uint32_t k,
+                          const Rule &R, cudaStream_t st, const uint64_t *t_dev = nullptr);
+bool tblock_plan(uint32_t L, uint32_t k, uint32_t *nslabs, size_t *smem);
 bool fused_shape_ok(uint32_t L, int V, int ring);
 size_t fused_smem_bytes(uint32_t L);
 
@@ -92,6 +96,8 @@ struct sca_sim {
     uint64_t t;
     int kernel;
     int fused_V, fused_ring;          // fused launch shape (0 = default)
+    int tb_k;                         // MCS per temporal-blocking launch
+    bool tb_set;                      // tb_k chosen by the caller (else automatic)
     bool timing;
     std::vector<cudaEvent_t> ev;      // start/stop pairs around update launches
     uint64_t timed_launches;
@@ -101,6 +107,8 @@ struct sca_sim {
 namespace sca {
 int make_rule(const sca_params &prm, Rule &R);
 bool use_fused(const sca_sim *s);
+// Kernel actually used (1 two-pass, 2 fused, 3 temporal blocking) and, for 3, MCS per launch.
+int effective_kernel(const sca_sim *s, int *tb_k);
 int step_impl(sca_sim *s, uint64_t n);
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *where);

@@ -114,10 +114,19 @@ static cudaError_t capture_chunk(ServeReq *r, cudaStream_t st)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    const bool fused = use_fused(s);
+    int tbk = 0;
+    const int kern = effective_kernel(s, &tbk);
+    const bool fused = kern == 2;
     int cur = s->cur;
     cudaError_t le = cudaSuccess;
-    for (uint32_t i = 0; i < kChunk && le == cudaSuccess; ++i) {
+    if (kern == 3) {                           // temporal blocking: kChunk / tbk launches
+        for (uint32_t i = 0; i < kChunk && le == cudaSuccess; i += (uint32_t)tbk) {
+            le = launch_tblock(s->buf[cur], s->buf[cur ^ 1], s->L, i, (uint32_t)tbk, s->R, st,
+                               r->t_dev);
+            cur ^= 1;
+        }
+    }
+    for (uint32_t i = 0; kern != 3 && i < kChunk && le == cudaSuccess; ++i) {
         if (fused) {
             le = launch_fused_mcs(s->buf[cur], s->buf[cur ^ 1], s->L, i, s->R, s->err, st, r->t_dev,
                                   s->fused_V, s->fused_ring);
@@ -231,9 +240,21 @@ static int enqueue_piece(sca_server *srv, ServeReq *r)
             for (uint64_t c = 0; c < k; ++c) {
                 e = cudaGraphLaunch(r->chunk[s->cur], sl.stream);
                 if (e != cudaSuccess) return cuda_fail(e, "graph launch");
-                count_launches(kChunk * (use_fused(s) ? 1 : 2) + 1);
+                {
+                    int tk = 0;
+                    const int kk = effective_kernel(s, &tk);
+                    count_launches((kk == 3 ? kChunk / (uint32_t)tk : kChunk * (kk == 2 ? 1 : 2)) + 1);
+                }
             }
-            s->t += k * kChunk;       // fused: kChunk is even, so the state buffer is unchanged
+            s->t += k * kChunk;
+            {
+                // each graph replay swaps the state buffers once per launch that writes the
+                // other buffer: kChunk times (fused) or kChunk / tbk times (temporal blocking)
+                int tk = 0;
+                const int kk = effective_kernel(s, &tk);
+                const uint32_t swaps = kk == 2 ? kChunk : kk == 3 ? kChunk / (uint32_t)tk : 0u;
+                if (swaps & 1u) s->cur ^= (int)(k & 1u);
+            }
         } else {
             int rc = step_impl(s, gap);
             if (rc) return rc;

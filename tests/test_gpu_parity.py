@@ -282,3 +282,36 @@ def test_fused_launch_shapes_agree(sca, L, shape):
     assert res[0][0] == res[1][0]
     import torch
     assert torch.equal(res[0][1], res[1][1])
+
+
+@pytest.mark.parametrize("L,p,q,mode,k", [
+    (128, 0.75, 0.25, 1, 4), (192, 0.875, 0.125, 1, 2), (320, 0.7, 0.3, 2, 4),
+    (1024, 0.5, 0.0, 1, 8), (4096, 0.75, 0.25, 1, 4), (8192, 0.95, 0.05, 2, 2),
+    (2048, 1.0, 0.0, 1, 16), (640, 0.5, 0.5, 1, 1),
+])
+def test_temporal_blocking_equals_two_pass(sca, L, p, q, mode, k):
+    """Several MCS per launch in shared memory (with recomputed halos) give the same states and
+    sums as the two-pass kernel, also when the run length is not a multiple of k."""
+    times = sorted({1, 3, k + 1, 2 * k + 3})
+    res = []
+    for kernel in (sca.KERNEL_TWO_PASS, sca.KERNEL_TBLOCK):
+        with sca.Sim(L, seed=23, p=p, q=q, rng=mode) as sim:
+            if kernel == sca.KERNEL_TBLOCK:
+                sim.set_temporal_block(k)
+            sim.set_kernel(kernel)
+            assert sim.kernel_in_use() == kernel
+            obs = sim.run(times)
+            res.append(([(o.S1, o.S2, o.num) for o in obs], sim.get_state()))
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1])
+
+
+def test_temporal_blocking_against_oracle(sca):
+    L, seed, p, q = 256, 4, 0.625, 0.375
+    times = [2, 4, 9]
+    with sca.Sim(L, seed=seed, p=p, q=q, kernel=sca.KERNEL_TBLOCK) as sim:
+        obs = sim.run(times)
+        words = sim.get_state()
+    words_o, ora = oracle_run_obs(L, seed, p, q, times)
+    assert_obs_equal(obs, ora)
+    assert np.array_equal(words, words_o)

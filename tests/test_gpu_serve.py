@@ -153,3 +153,19 @@ def test_request_stream_sample_against_oracle(sca):
             t = x.t
             ref = o.observe(bx, by)
             assert (x.S1, x.S2, x.num) == (ref["S1"], ref["S2"], ref["num"]), (r, x.t)
+
+
+def test_served_kernels_agree(sca):
+    """Requests whose lattice runs with temporal blocking (small L), the two-pass kernel (per-site
+    uniforms at L = 4096) and the fused kernel (dyadic, L = 32768) all equal a single simulation
+    with the kernel fixed to two-pass."""
+    reqs = [dict(L=512, p=0.75, q=0.25, seed=3, n=200), dict(L=1024, p=0.7, q=0.3, seed=4, n=130),
+            dict(L=4096, p=0.6, q=0.4, seed=5, n=66), dict(L=32768, p=0.5, q=0.0, seed=6, n=66)]
+    with sca.Server(budget_bytes=8 << 30, max_active=4, max_L=32768) as srv:
+        tks = [srv.submit(r["L"], r["p"], r["q"], r["seed"], r["n"]) for r in reqs]
+        res = [srv.wait(tk, 300000) for tk in tks]
+    for r, (rc, obs, _) in zip(reqs, res):
+        assert rc == sca.OK
+        with sca.Sim(r["L"], seed=r["seed"], p=r["p"], q=r["q"], kernel=sca.KERNEL_TWO_PASS) as sim:
+            ref = sim.run([x.t for x in obs])
+        assert key(obs) == key(ref), r
