@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-mcs", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    ap.add_argument("--ref-seconds", type=float, default=None,
+                    help="seconds of oracle work per reference-arm step (default: about a "
+                         "minute in total, 2 to 20 s per step)")
     return ap.parse_args()
 
 
@@ -170,6 +173,20 @@ def recorded_traffic(kernel_name, L):
         "bytes_per_launch_at_L", {}) else None
 
 
+# ----------------------------------------------------------------------------- replicas
+def aggregate_replicas(local_updates, local_seconds, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank's updates summed, divided by
+    the slowest rank's time (max over ranks).  Returns (updates_per_s, max_seconds)."""
+    if dist is None:
+        return local_updates / local_seconds, local_seconds
+    import torch
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 # ----------------------------------------------------------------------------- oracle arm
 def oracle_sample(L, p, q, seconds, seed=1):
     """Time the CPU oracle on a band of rows of the same lattice (full width L), enough MCS
@@ -195,7 +212,9 @@ def oracle_sample(L, p, q, seconds, seed=1):
 def run_reference(a, rank, world):
     if rank != 0:
         return
-    per_step = max(2.0, min(20.0, 60.0 / max(1, a.steps + a.warmup)))
+    per_step = a.ref_seconds
+    if per_step is None:
+        per_step = max(2.0, min(20.0, 60.0 / max(1, a.steps + a.warmup)))
     for _ in range(a.warmup):
         oracle_sample(a.L, a.p, a.q, per_step / 4)
     rates, descs, cores = [], [], 1
@@ -390,11 +409,8 @@ def run_ours(a, rank, world, local_rank):
     upd_ms, upd_launches = sim.timing_read()
     sim.timing(False)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = updates_per_step * a.steps * world / (ms / 1000.0)
+    value, secs = aggregate_replicas(updates_per_step * a.steps, ms / 1000.0, dist, dev)
+    ms = secs * 1000.0
 
     # roofline of the dominant (update) kernel, timed live over the same region
     fused = (sim.kernel_in_use() == sca.KERNEL_FUSED)
@@ -436,12 +452,9 @@ def run_ours(a, rank, world, local_rank):
             e2e_step()
         sync_all()
         e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_value, e2e_s = aggregate_replicas(updates_per_step * a.steps, e2e_s, dist, dev)
         obs_bytes = len(times) * 72
-        e2e = {"value": updates_per_step * a.steps * world / e2e_s, "unit": UNIT,
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 4 * n_words, "d2h_bytes_per_step": 4 * n_words + obs_bytes,
                "ms_per_step": 1000.0 * e2e_s / a.steps}
 
