@@ -130,11 +130,14 @@ int sca_run(sca_sim *sim, const uint64_t *times, uint32_t n, sca_obs *out);
 int sca_get_state(sca_sim *sim, uint32_t *host_words, size_t n_words);
 
 /* Replace the state by n_words = 4 * L * L/64 canonical words from host memory and set the
- * MCS count to t (the next step uses MCS index t); synchronises.  The words are not checked
- * here; sca_observe reports a state that does not close. */
+ * MCS count to t (the next step uses MCS index t); synchronises.  The words are accepted as
+ * they are; one device pass records whether they form a surface (every plaquette closes and
+ * the slopes sum to zero around the torus), which kernel 4 of sca_set_kernel requires, and
+ * sca_observe reports a state that does not close. */
 int sca_set_state(sca_sim *sim, const uint32_t *host_words, size_t n_words, uint64_t t);
 
-/* Device pointer to the current canonical words (valid until the next call on sim). */
+/* Device pointer to the current canonical words (valid until the next call on sim).  Read
+ * only: write a new state with sca_set_state. */
 int sca_state_device(sca_sim *sim, uint32_t **words_dev);
 
 /* MCS completed so far. */
@@ -145,14 +148,26 @@ uint64_t sca_time(const sca_sim *sim);
  * per-site uniforms up to L = 2048; else two-pass), 1 = two-pass (one launch per sublattice, the
  * paper's Fig. 3 structure), 2 = fused even+odd wavefront (one launch per MCS; needs L a
  * multiple of 2048), 3 = temporal blocking (several MCS per launch in shared memory, see
- * sca_set_temporal_block).  Results are identical for every choice; only speed differs.
- * Errors: SCA_EINVAL. */
+ * sca_set_temporal_block), 4 = register-wavefront temporal blocking (each warp streams a band
+ * of rows through registers as one height bit per site and advances it up to 16 MCS per launch
+ * with {0, 1} probabilities, 4 with dyadic draws; per-site uniform draws are not supported, and
+ * sca_step returns SCA_ESTATE if the state is not a surface, see sca_set_state).
+ * Results are identical for every choice; only speed differs.
+ * Errors: SCA_EINVAL (unknown kernel, or one that does not support this lattice or rule). */
 int sca_set_kernel(sca_sim *sim, int kernel);
 
-/* Temporal blocking (kernel 3 of sca_set_kernel): each launch advances mcs_per_launch MCS
- * (a divisor of 64; 0 = default 4) with every CTA's rows and a halo of 2 rows per MCS held in
- * shared memory.  Errors: SCA_EINVAL if the slab with its halo does not fit for this L. */
+/* Temporal blocking (kernels 3 and 4 of sca_set_kernel): each launch advances mcs_per_launch
+ * MCS (a divisor of 64; 0 = default: 4 for kernel 3, the most kernel 4 supports for the rule)
+ * with a halo of 2 rows per MCS above and below every block of rows; kernel 4 caps a launch at
+ * 16 MCS ({0, 1} probabilities) or 4 (dyadic draws).  Errors: SCA_EINVAL if mcs_per_launch
+ * does not divide 64 or, for kernel 3, the block with its halo does not fit for this L. */
 int sca_set_temporal_block(sca_sim *sim, int mcs_per_launch);
+
+/* Row bands of the register-wavefront kernel (kernel 4): the lattice is cut into `bands` bands
+ * of rows times columns of 30 packed words, one warp per tile; 0 = automatic (enough tiles for
+ * one full wave of resident warps).  Results do not depend on it.  Errors: SCA_EINVAL unless
+ * 0 <= bands <= L/2. */
+int sca_set_wave_bands(sca_sim *sim, int bands);
 
 /* Launch shape of the fused kernel: words_per_thread (1, 2 or 4; the CTA has L/64 /
  * words_per_thread threads, 32..512) and ring = lattice rows held in shared memory (6; or 8 or
@@ -161,8 +176,8 @@ int sca_set_temporal_block(sca_sim *sim, int mcs_per_launch);
  * on the shape.  Errors: SCA_EINVAL if the shape does not fit L. */
 int sca_set_fused_shape(sca_sim *sim, int words_per_thread, int ring);
 
-/* Update kernel the simulation uses now (1 = two-pass, 2 = fused, 3 = temporal blocking), after
- * automatic choice. */
+/* Update kernel the simulation uses now (1 = two-pass, 2 = fused, 3 = temporal blocking in
+ * shared memory, 4 = register-wavefront temporal blocking), after automatic choice. */
 int sca_get_kernel(const sca_sim *sim);
 
 /* Kernel timing: while enabled, the library records a CUDA event pair on the simulation's

@@ -139,6 +139,8 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
     s->fused_ring = 0;
     s->tb_k = 4;
     s->tb_set = false;
+    s->wave_bands = 0;
+    s->surface = true;
     s->cur = 0;
     s->timing = false;
     s->timed_launches = 0;
@@ -195,12 +197,13 @@ int sca_reset(sca_sim *s)
     if (e == cudaSuccess) e = cudaMemsetAsync((char *)s->buf[s->cur] + half, 0xFF, half, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     s->t = 0;
+    s->surface = true;
     return SCA_OK;
 }
 
 int sca_set_kernel(sca_sim *s, int kernel)
 {
-    if (!s || kernel < 0 || kernel > 3) return fail(SCA_EINVAL, "kernel must be 0, 1, 2 or 3");
+    if (!s || kernel < 0 || kernel > 4) return fail(SCA_EINVAL, "kernel must be 0, 1, 2, 3 or 4");
     if (kernel == 2 && !fused_supported(s->L))
         return fail(SCA_EINVAL, "fused kernel needs L to be a multiple of 2048");
     if (kernel == 3) {
@@ -209,7 +212,20 @@ int sca_set_kernel(sca_sim *s, int kernel)
         if (!tblock_plan(s->L, (uint32_t)s->tb_k, &ns, &sm))
             return fail(SCA_EINVAL, "temporal blocking does not fit this lattice size");
     }
+    if (kernel == 4) {
+        if (s->R.mode == 2) return fail(SCA_EINVAL, "the wavefront kernel takes dyadic draws only");
+        if (!wave_supported(s->L, (uint32_t)wave_max_k((int)s->R.mode), (int)s->R.mode))
+            return fail(SCA_EINVAL, "the wavefront kernel does not fit this lattice size");
+    }
     s->kernel = kernel;
+    return SCA_OK;
+}
+
+int sca_set_wave_bands(sca_sim *s, int bands)
+{
+    if (!s || bands < 0 || (uint32_t)bands > s->L / 2)
+        return fail(SCA_EINVAL, "bands must be 0 (automatic) or 1..L/2");
+    s->wave_bands = (uint32_t)bands;
     return SCA_OK;
 }
 
@@ -218,6 +234,11 @@ int sca_set_temporal_block(sca_sim *s, int mcs_per_launch)
     if (!s) return fail(SCA_EINVAL, "NULL simulation");
     const int k = mcs_per_launch > 0 ? mcs_per_launch : 4;
     if (k > 64 || (64 % k) != 0) return fail(SCA_EINVAL, "MCS per launch must divide 64");
+    if (s->kernel == 4) {               // launches of the largest supported power of two <= k
+        s->tb_k = k;
+        s->tb_set = true;
+        return SCA_OK;
+    }
     uint32_t ns;
     size_t sm;
     if (!tblock_plan(s->L, (uint32_t)k, &ns, &sm))
@@ -238,6 +259,8 @@ int sca::effective_kernel(const sca_sim *s, int *tb_k)
 {
     int k = s->kernel;
     int kk = s->tb_k;
+    if (k == 4) kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : (uint32_t)wave_max_k((int)s->R.mode),
+                                      (int)s->R.mode);
     if (k == 0) {
         uint32_t ns;
         size_t sm;
@@ -299,7 +322,9 @@ int sca::step_impl(sca_sim *s, uint64_t n)
     int tbk = 0;
     const int kern = effective_kernel(s, &tbk);
     const bool fused = kern == 2;
-    if (kern == 3) {                           // temporal blocking: tbk MCS per launch
+    if (kern == 4 && !s->surface)
+        return fail(SCA_ESTATE, "the wavefront kernel needs a surface state (every plaquette closes)");
+    if (kern == 3 || kern == 4) {              // temporal blocking: tbk MCS per launch
         if (s->timing) {
             cudaError_t e = record_event(s);
             if (e != cudaSuccess) return cuda_fail(e, "timing event");
@@ -307,14 +332,18 @@ int sca::step_impl(sca_sim *s, uint64_t n)
         uint64_t done = 0, launches = 0;
         while (done < n) {
             const uint64_t k = (n - done) < (uint64_t)tbk ? (n - done) : (uint64_t)tbk;
-            cudaError_t e = launch_tblock(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->t + done,
-                                          (uint32_t)k, s->R, s->stream);
+            const uint64_t kk = kern == 3 ? k : wave_pick_k((uint32_t)k, (int)s->R.mode);
+            cudaError_t e = kern == 3
+                ? launch_tblock(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->t + done, (uint32_t)k,
+                                s->R, s->stream)
+                : launch_wave(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->t + done, (uint32_t)kk,
+                              s->R, s->stream, nullptr, s->wave_bands);
             if (e != cudaSuccess) {
                 s->t += done;
                 return cuda_fail(e, "temporal-blocking launch");
             }
             s->cur ^= 1;
-            done += k;
+            done += kern == 3 ? k : kk;
             ++launches;
         }
         s->t += n;
@@ -434,6 +463,10 @@ int sca_set_state(sca_sim *s, const uint32_t *host_words, size_t n_words, uint64
                                     cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sca_set_state");
+    bool surf = false;
+    e = surface_check(s->buf[s->cur], s->L, reinterpret_cast<uint32_t *>(s->part), s->stream, &surf);
+    if (e != cudaSuccess) return cuda_fail(e, "surface check");
+    s->surface = surf;
     s->t = t;
     return SCA_OK;
 }

@@ -55,6 +55,19 @@ cudaError_t launch_wait_selftest(long long limit_cycles, uint32_t *err, cudaStre
 cudaError_t launch_tblock(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t0, uint32_t k,
                           const Rule &R, cudaStream_t st, const uint64_t *t_dev = nullptr);
 bool tblock_plan(uint32_t L, uint32_t k, uint32_t *nslabs, size_t *smem);
+// Register-wavefront temporal blocking on height bits: k MCS per launch (a power of two up to
+// wave_max_k(mode)), src -> dst (ping-pong); bands of rows per column of tiles (0 = automatic).
+// Needs a surface state (surface_check); dyadic and {0,1} probabilities only.
+cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t0, uint32_t k,
+                        const Rule &R, cudaStream_t st, const uint64_t *t_dev = nullptr,
+                        uint32_t bands = 0);
+bool wave_supported(uint32_t L, uint32_t k, int mode);
+int wave_max_k(int mode);
+uint32_t wave_pick_k(uint32_t want, int mode);   // largest supported power of two <= want
+// Is A a surface (every plaquette closes, row 0 and column 0 close around the torus)?  Uses 3
+// words of device scratch; synchronises the stream.
+cudaError_t surface_check(const uint32_t *A, uint32_t L, uint32_t *scratch, cudaStream_t st,
+                          bool *is_surface);
 bool fused_shape_ok(uint32_t L, int V, int ring);
 size_t fused_smem_bytes(uint32_t L);
 
@@ -98,6 +111,8 @@ struct sca_sim {
     int fused_V, fused_ring;          // fused launch shape (0 = default)
     int tb_k;                         // MCS per temporal-blocking launch
     bool tb_set;                      // tb_k chosen by the caller (else automatic)
+    uint32_t wave_bands;              // row bands of the register-wavefront kernel (0 = auto)
+    bool surface;                     // the state is known to be a surface (kernel 4 needs it)
     bool timing;
     std::vector<cudaEvent_t> ev;      // start/stop pairs around update launches
     uint64_t timed_launches;
@@ -107,7 +122,8 @@ struct sca_sim {
 namespace sca {
 int make_rule(const sca_params &prm, Rule &R);
 bool use_fused(const sca_sim *s);
-// Kernel actually used (1 two-pass, 2 fused, 3 temporal blocking) and, for 3, MCS per launch.
+// Kernel actually used (1 two-pass, 2 fused, 3 shared-memory temporal blocking, 4 register
+// wavefront) and, for 3 and 4, MCS per launch.
 int effective_kernel(const sca_sim *s, int *tb_k);
 int step_impl(sca_sim *s, uint64_t n);
 int fail(int code, const std::string &msg);

@@ -119,14 +119,17 @@ static cudaError_t capture_chunk(ServeReq *r, cudaStream_t st)
     const bool fused = kern == 2;
     int cur = s->cur;
     cudaError_t le = cudaSuccess;
-    if (kern == 3) {                           // temporal blocking: kChunk / tbk launches
+    const bool tb = kern == 3 || kern == 4;
+    if (tb) {                                  // temporal blocking: kChunk / tbk launches
         for (uint32_t i = 0; i < kChunk && le == cudaSuccess; i += (uint32_t)tbk) {
-            le = launch_tblock(s->buf[cur], s->buf[cur ^ 1], s->L, i, (uint32_t)tbk, s->R, st,
-                               r->t_dev);
+            le = kern == 3 ? launch_tblock(s->buf[cur], s->buf[cur ^ 1], s->L, i, (uint32_t)tbk, s->R,
+                                           st, r->t_dev)
+                           : launch_wave(s->buf[cur], s->buf[cur ^ 1], s->L, i, (uint32_t)tbk, s->R,
+                                         st, r->t_dev, s->wave_bands);
             cur ^= 1;
         }
     }
-    for (uint32_t i = 0; kern != 3 && i < kChunk && le == cudaSuccess; ++i) {
+    for (uint32_t i = 0; !tb && i < kChunk && le == cudaSuccess; ++i) {
         if (fused) {
             le = launch_fused_mcs(s->buf[cur], s->buf[cur ^ 1], s->L, i, s->R, s->err, st, r->t_dev,
                                   s->fused_V, s->fused_ring);
@@ -243,7 +246,7 @@ static int enqueue_piece(sca_server *srv, ServeReq *r)
                 {
                     int tk = 0;
                     const int kk = effective_kernel(s, &tk);
-                    count_launches((kk == 3 ? kChunk / (uint32_t)tk : kChunk * (kk == 2 ? 1 : 2)) + 1);
+                    count_launches((kk >= 3 ? kChunk / (uint32_t)tk : kChunk * (kk == 2 ? 1 : 2)) + 1);
                 }
             }
             s->t += k * kChunk;
@@ -252,7 +255,7 @@ static int enqueue_piece(sca_server *srv, ServeReq *r)
                 // other buffer: kChunk times (fused) or kChunk / tbk times (temporal blocking)
                 int tk = 0;
                 const int kk = effective_kernel(s, &tk);
-                const uint32_t swaps = kk == 2 ? kChunk : kk == 3 ? kChunk / (uint32_t)tk : 0u;
+                const uint32_t swaps = kk == 2 ? kChunk : kk >= 3 ? kChunk / (uint32_t)tk : 0u;
                 if (swaps & 1u) s->cur ^= (int)(k & 1u);
             }
         } else {

@@ -1,0 +1,171 @@
+// Register-wavefront temporal blocking: host side, {0, 1}-probability instantiations and the
+// surface check the height-bit representation relies on (kernel in sca_wave.cuh; dyadic
+// instantiations in sca_wave_dyadic.cu).
+#include "sca_wave.cuh"
+
+namespace sca {
+
+// Dyadic instantiations (other translation unit, compiled in parallel).
+cudaError_t launch_wave_dyadic(const WaveArgs &a, int K, int grid, cudaStream_t st);
+int wave_dyadic_blocks_per_sm(int K);
+
+template <int K, bool DP, bool DQ>
+static int blocks_per_sm()
+{
+    static int n = 0;
+    if (n == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wave<K, 0, DP, DQ>, 32 * kWaveWarps, 0) !=
+                cudaSuccess || b <= 0)
+            b = 1;
+        n = b;
+    }
+    return n;
+}
+
+template <int K>
+static int blocks_mode0(bool dp, bool dq)
+{
+    if (dp && dq) return blocks_per_sm<K, true, true>();
+    if (dp) return blocks_per_sm<K, true, false>();
+    if (dq) return blocks_per_sm<K, false, true>();
+    return blocks_per_sm<K, false, false>();
+}
+
+template <int K>
+static cudaError_t launch_mode0(const WaveArgs &a, int grid, cudaStream_t st)
+{
+    const bool dp = a.R.Pp != 0, dq = a.R.Pq != 0;
+    if (dp && dq) k_wave<K, 0, true, true><<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else if (dp) k_wave<K, 0, true, false><<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else if (dq) k_wave<K, 0, false, true><<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else k_wave<K, 0, false, false><<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int wave_max_k(int mode) { return mode == 0 ? 16 : mode == 1 ? 4 : 0; }
+
+uint32_t wave_pick_k(uint32_t want, int mode)
+{
+    uint32_t k = 1;
+    const uint32_t cap = (uint32_t)wave_max_k(mode);
+    while (2 * k <= want && 2 * k <= cap) k *= 2;
+    return cap ? k : 0;
+}
+
+static int blocks_for(int K, const Rule &R)
+{
+    if (R.mode == 1) return wave_dyadic_blocks_per_sm(K);
+    const bool dp = R.Pp != 0, dq = R.Pq != 0;
+    switch (K) {
+    case 1: return blocks_mode0<1>(dp, dq);
+    case 2: return blocks_mode0<2>(dp, dq);
+    case 4: return blocks_mode0<4>(dp, dq);
+    case 8: return blocks_mode0<8>(dp, dq);
+    default: return blocks_mode0<16>(dp, dq);
+    }
+}
+
+// Bands of rows: enough tiles (warps) for one full wave of resident warps, but bands of at
+// least 8K rows so the recomputed halo stays at most half of the streamed rows.
+static bool wave_plan(uint32_t L, uint32_t k, int mode, uint32_t bands, int blocks_per_sm,
+                      uint32_t *nbands, uint32_t *ncols)
+{
+    if (L < 64 || L % 64 != 0 || k == 0 || (k & (k - 1)) != 0) return false;
+    if ((int)k > wave_max_k(mode)) return false;
+    const uint32_t W = L / 64;
+    const uint32_t nc = (W + kWaveTileWords - 1) / kWaveTileWords;
+    uint32_t nb = bands;
+    if (nb == 0) {
+        const uint64_t warps = (uint64_t)sm_count() * blocks_per_sm * kWaveWarps;
+        nb = (uint32_t)((warps + nc / 2) / nc);
+        const uint32_t cap = L / (8u * k);
+        if (nb > cap) nb = cap;
+        if (nb == 0) nb = 1;
+    }
+    if (nb > L / 2) return false;
+    *nbands = nb;
+    *ncols = nc;
+    return true;
+}
+
+bool wave_supported(uint32_t L, uint32_t k, int mode)
+{
+    uint32_t nb, nc;
+    return wave_plan(L, wave_pick_k(k, mode), mode, 0, 1, &nb, &nc);
+}
+
+cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t0, uint32_t k,
+                        const Rule &R, cudaStream_t st, const uint64_t *t_dev, uint32_t bands)
+{
+    const int mode = (int)R.mode;
+    uint32_t nb, nc;
+    if (!wave_plan(L, k, mode, bands, 1, &nb, &nc)) return cudaErrorInvalidValue;
+    if (!wave_plan(L, k, mode, bands, blocks_for((int)k, R), &nb, &nc)) return cudaErrorInvalidValue;
+    const WaveArgs a{src, dst, L, L / 64, nb, nc, t0, t_dev, R};
+    const uint64_t tiles = (uint64_t)nb * nc;
+    const int grid = (int)((tiles + kWaveWarps - 1) / kWaveWarps);
+    count_launches(1);
+    if (mode == 1) return launch_wave_dyadic(a, (int)k, grid, st);
+    switch (k) {
+    case 1: return launch_mode0<1>(a, grid, st);
+    case 2: return launch_mode0<2>(a, grid, st);
+    case 4: return launch_mode0<4>(a, grid, st);
+    case 8: return launch_mode0<8>(a, grid, st);
+    case 16: return launch_mode0<16>(a, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------------------------------ surface check
+// A state is a surface when every plaquette closes and the slopes sum to zero around the torus
+// along row 0 and column 0 (then along every row and column).  For the plaquette with corners
+// (x-1, y-1) and (x, y): sx-(x, y) - sx-(x, y-1) == sy-(x, y) - sy-(x-1, y), i.e. with slope
+// bits a, b, c, d: a + d == b + c.  One thread per canonical word of sublattice s, row y.
+__global__ void k_surface_check(const uint32_t *A, uint32_t L, uint32_t W, uint32_t *out)
+{
+    const size_t plane = (size_t)L * W;
+    const size_t n = 2 * plane;
+    for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t s = (uint32_t)(w / plane);
+        const size_t rem = w - (size_t)s * plane;
+        const uint32_t y = (uint32_t)(rem / W), j = (uint32_t)(rem - (size_t)y * W);
+        const uint32_t ns = s ^ 1u, yp = y == 0 ? L - 1 : y - 1, jp = j == 0 ? W - 1 : j - 1;
+        const uint32_t *SXs = A + (size_t)(2 * s) * plane, *SYs = A + (size_t)(2 * s + 1) * plane;
+        const uint32_t *SXn = A + (size_t)(2 * ns) * plane, *SYn = A + (size_t)(2 * ns + 1) * plane;
+        const uint32_t a = SXs[(size_t)y * W + j];
+        const uint32_t b = SXn[(size_t)yp * W + j];
+        const uint32_t c = SYs[(size_t)y * W + j];
+        const uint32_t dn = SYn[(size_t)y * W + j];
+        // the site left of x is bit k of the other sublattice when this row sits right
+        // ((s + y) odd), else bit k - 1
+        const uint32_t d = ((s + y) & 1u) ? dn : __funnelshift_l(SYn[(size_t)y * W + jp], dn, 1);
+        const uint32_t bad = ((a ^ d) ^ (b ^ c)) | ((a & d) ^ (b & c));
+        if (bad) atomicOr(out, 1u);
+        if (y == 0) atomicAdd(out + 1, (uint32_t)__popc(a));
+        if (j == 0 && s == (y & 1u)) atomicAdd(out + 2, c & 1u);
+    }
+}
+
+cudaError_t surface_check(const uint32_t *A, uint32_t L, uint32_t *scratch, cudaStream_t st,
+                          bool *is_surface)
+{
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const uint32_t W = L / 64;
+    const size_t n = 2 * (size_t)L * W;
+    int grid = (int)((n + 255) / 256);
+    if (grid > sm_count() * 8) grid = sm_count() * 8;
+    k_surface_check<<<grid, 256, 0, st>>>(A, L, W, scratch);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    uint32_t h[3];
+    e = cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    *is_surface = h[0] == 0 && h[1] == L / 2 && h[2] == L / 2;
+    return cudaSuccess;
+}
+
+}  // namespace sca

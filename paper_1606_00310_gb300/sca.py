@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(PKG, "libsca.so")
 OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT, EBUSY, ESTATE, ENOTFOUND, ECANCELED = \
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 RNG_AUTO, RNG_DYADIC, RNG_UNIFORM32 = 0, 1, 2
-KERNEL_AUTO, KERNEL_TWO_PASS, KERNEL_FUSED, KERNEL_TBLOCK = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_TWO_PASS, KERNEL_FUSED, KERNEL_TBLOCK, KERNEL_WAVE = 0, 1, 2, 3, 4
 
 
 class sca_params(C.Structure):
@@ -61,6 +61,7 @@ SIGNATURES = {
     "sca_get_kernel": (C.c_int, [C.c_void_p]),
     "sca_set_fused_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "sca_set_temporal_block": (C.c_int, [C.c_void_p, C.c_int]),
+    "sca_set_wave_bands": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     "sca_free": (None, [C.c_void_p]),
@@ -214,6 +215,9 @@ class Sim:
 
     def set_temporal_block(self, mcs_per_launch: int):
         check(load().sca_set_temporal_block(self._h, int(mcs_per_launch)), "sca_set_temporal_block")
+
+    def set_wave_bands(self, bands: int):
+        check(load().sca_set_wave_bands(self._h, int(bands)), "sca_set_wave_bands")
 
     def set_fused_shape(self, words_per_thread: int, ring: int):
         check(load().sca_set_fused_shape(self._h, int(words_per_thread), int(ring)),

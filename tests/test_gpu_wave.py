@@ -1,0 +1,114 @@
+"""Register-wavefront temporal blocking (kernel 4) vs the two-pass kernel and the CPU oracle.
+
+Several MCS per launch with each warp streaming a band of rows through registers; tiles
+recompute halo words and rows.  Integer work: states and sums must be identical to the
+two-pass kernel's and the oracle's.  Cases span one-word rows (W = 1), odd word counts, column
+tiles that wrap around the lattice, two-row bands, uneven bands, run lengths that are not a
+multiple of the MCS per launch (so shorter launches of 1..k-1 MCS), and the full-size
+L = 65536 lattice.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sca():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_00310_gb300 import build
+    build.build()
+    import paper_1606_00310_gb300.sca as mod
+    mod.load()
+    return mod
+
+
+def _run(sca, kernel, L, p, q, times, k=None, bands=None, seed=23):
+    with sca.Sim(L, seed=seed, p=p, q=q) as sim:
+        sim.set_kernel(kernel)
+        if k is not None:
+            sim.set_temporal_block(k)
+        if bands is not None:
+            sim.set_wave_bands(bands)
+        assert sim.kernel_in_use() == kernel
+        obs = sim.run(times)
+        return [(g.S1, g.S2, g.num) for g in obs], sim.get_state()
+
+
+WAVE_CASES = [
+    (64, 0.75, 0.25, 4, 0), (128, 1.0, 0.0, 8, 0), (192, 0.875, 0.125, 4, 0),
+    (320, 0.5, 0.5, 8, 7), (2048, 0.75, 0.25, 8, 0), (1984, 0.625, 0.0, 2, 992),
+    (4096, 1.0, 0.0, 8, 0), (4096, 0.5, 0.0, 1, 0), (8192, 0.9375, 0.0625, 8, 3),
+    (6144, 1.0, 1.0, 4, 0), (3968, 0.75, 0.25, 2, 5),
+]
+
+
+@pytest.mark.parametrize("L,p,q,k,bands", WAVE_CASES)
+def test_wave_equals_two_pass(sca, L, p, q, k, bands):
+    times = sorted({1, 3, k + 1, 2 * k + 3, 20})
+    ref = _run(sca, sca.KERNEL_TWO_PASS, L, p, q, times)
+    got = _run(sca, sca.KERNEL_WAVE, L, p, q, times, k=k, bands=bands)
+    assert ref[0] == got[0]
+    assert np.array_equal(ref[1], got[1])
+
+
+@pytest.mark.parametrize("L,p,q,times", [(256, 0.625, 0.375, [2, 4, 9]),
+                                         (320, 0.75, 0.0, [1, 8, 17]),
+                                         (448, 1.0, 0.5, [5, 13])])
+def test_wave_against_oracle(sca, L, p, q, times):
+    seed = 4
+    with sca.Sim(L, seed=seed, p=p, q=q, kernel=sca.KERNEL_WAVE) as sim:
+        obs = sim.run(times)
+        words = sim.get_state()
+    bx, by = o.init_flat(L)
+    t = 0
+    for tt, g in zip(times, obs):
+        o.run(bx, by, seed, p, q, t0=t, n_mcs=tt - t)
+        t = tt
+        r = o.observe(bx, by)
+        assert g.status == 0
+        assert (g.S1, g.S2, g.num, g.N) == (r["S1"], r["S2"], r["num"], r["N"])
+    assert np.array_equal(words, o.pack(bx, by))
+
+
+@pytest.mark.parametrize("p,q", [(0.75, 0.25), (0.5, 0.0)])
+def test_wave_full_size_equals_fused(sca, p, q):
+    """L = 65536 (1 GiB of packed slopes), the automatic band count: identical device states
+    and sums to the fused kernel after runs of 1, 3, 8 and 11 MCS."""
+    import torch
+    times = [1, 3, 8, 11]
+    res = []
+    for kernel in (sca.KERNEL_FUSED, sca.KERNEL_WAVE):
+        with sca.Sim(65536, seed=9, p=p, q=q, kernel=kernel) as sim:
+            obs = sim.run(times)
+            res.append(([(g.S1, g.S2, g.num) for g in obs], sim.state_tensor().clone()))
+    assert res[0][0] == res[1][0]
+    assert torch.equal(res[0][1], res[1][1])
+
+
+def test_wave_full_size_p1_closed_form(sca):
+    """L = 65536, p = 1, q = 0: flat again after every MCS, num = N^2 / 4."""
+    import torch
+    with sca.Sim(65536, seed=1, p=1.0, q=0.0, kernel=sca.KERNEL_WAVE) as sim:
+        flat = sim.state_tensor().clone()
+        obs = sim.run([1, 2, 8, 24])
+        assert torch.equal(sim.state_tensor(), flat)
+    assert all(4 * g.num == g.N ** 2 for g in obs)
+
+
+def test_wave_rejects_what_it_cannot_run(sca):
+    with sca.Sim(256, seed=1, p=0.7, q=0.3, rng=sca.RNG_UNIFORM32) as sim:
+        with pytest.raises(sca.ScaError):
+            sim.set_kernel(sca.KERNEL_WAVE)
+    with sca.Sim(256, seed=1, p=0.75, q=0.25) as sim:
+        sim.set_kernel(sca.KERNEL_WAVE)
+        with pytest.raises(sca.ScaError):
+            sim.set_temporal_block(12)
+        with pytest.raises(sca.ScaError):
+            sim.set_wave_bands(-1)
+        with pytest.raises(sca.ScaError):
+            sim.set_wave_bands(129)
