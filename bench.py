@@ -35,12 +35,17 @@ METRIC = "site updates/s"
 UNIT = "updates/s"
 WORKLOAD = "octahedron SCA L=65536 p=1 q=0 flat, 1024 MCS, exact W^2 at 2^0..2^10"
 BYTES_PER_UPDATE = 0.5   # each slope bit read once and written once per MCS (roofline unit)
+# Height-bit wavefront kernel, one of p, q equal to 1 and the other 0: per 32-site word and
+# half-step, two 3-input logic ops fold the four neighbour comparisons, one applies the flip,
+# one funnel shift aligns the offset x-neighbour: 4 ALU-pipe ops per 32 site updates.
+WAVE_ALU_OPS_PER_UPDATE = 4.0 / 32.0
+ALU_LANES_PER_SM = 64    # 32-bit logic / shift results per clock per SM (4 SMSPs x 16 lanes)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--L", type=int, default=65536)
@@ -100,7 +105,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(gpu_index)],
+                 "-lms", "100", "-i", str(gpu_index)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -150,9 +155,26 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def alu_peak_tops(n_sm):
+    """Logic-op peak of the whole GPU in Tops/s: SMs x ALU lanes x maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        mhz = 2070.0
+    return n_sm * ALU_LANES_PER_SM * mhz * 1e6 / 1e12, mhz
+
+
+KERNEL_SOURCES = {
+    "k_fused_mcs": ("sca_update.cu", "sca_fused.cu", "sca_rng.cuh", "sca_internal.h"),
+    "k_half_step": ("sca_update.cu", "sca_fused.cu", "sca_rng.cuh", "sca_internal.h"),
+    "k_wave": ("sca_wave.cuh", "sca_wave.cu", "sca_rng.cuh", "sca_internal.h"),
+}
+
+
+def kernel_source_hash(kernel_name="k_fused_mcs"):
     h = hashlib.sha256()
-    for fn in ("sca_update.cu", "sca_fused.cu", "sca_rng.cuh", "sca_internal.h"):
+    for fn in KERNEL_SOURCES[kernel_name]:
         with open(os.path.join(ROOT, "paper_1606_00310_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -167,7 +189,7 @@ def recorded_traffic(kernel_name, L):
     except (OSError, ValueError):
         return None
     e = d.get(kernel_name)
-    if not e or e.get("src_sha256") != kernel_source_hash():
+    if not e or e.get("src_sha256") != kernel_source_hash(kernel_name):
         return None
     return float(e["bytes_per_launch_at_L"][str(L)]) if str(L) in e.get(
         "bytes_per_launch_at_L", {}) else None
@@ -413,20 +435,44 @@ def run_ours(a, rank, world, local_rank):
     ms = secs * 1000.0
 
     # roofline of the dominant (update) kernel, timed live over the same region
-    fused = (sim.kernel_in_use() == sca.KERNEL_FUSED)
-    kname = "k_fused_mcs" if fused else "k_half_step"
-    upd_per_launch = L * L if fused else L * L // 2
-    alg_bytes = BYTES_PER_UPDATE * upd_per_launch
-    avg_launch_s = upd_ms / 1000.0 / max(1, upd_launches)
+    kern = sim.kernel_in_use()
     peak, peak_src = peaks()
-    achieved = alg_bytes / avg_launch_s / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": recorded_traffic(kname, L),
-            "kernel": kname, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
-            if peak_src == "measured" else peak_src,
-            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
-            "update_share_of_step": upd_ms / ms if ms > 0 else None,
-            "updates_per_s_kernel_only": upd_per_launch / avg_launch_s}
+    upd_total = updates_per_step * a.steps
+    upd_s = upd_ms / 1000.0
+    avg_launch_s = upd_s / max(1, upd_launches)
+    one_rule = {a.p, a.q} == {0.0, 1.0}
+    if kern == sca.KERNEL_WAVE and one_rule:
+        # ALU-bound: algorithmic logic ops over the measured launch time
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        apeak, mhz = alu_peak_tops(n_sm)
+        achieved = WAVE_ALU_OPS_PER_UPDATE * upd_total / upd_s / 1e12
+        state_bytes = 0.5 * L * L           # canonical words: two slope bits per site
+        roof = {"bound": "alu", "achieved": achieved, "peak": apeak, "unit": "Tops/s",
+                "frac": achieved / apeak, "traffic": recorded_traffic("k_wave", L),
+                "kernel": "k_wave",
+                "peak_source": "derived: %d SMs x %d logic lanes/clk x %.0f MHz (max SM clock)"
+                               % (n_sm, ALU_LANES_PER_SM, mhz),
+                "alg_ops_per_update": WAVE_ALU_OPS_PER_UPDATE,
+                "avg_launch_ms": avg_launch_s * 1e3, "launches": upd_launches,
+                "mcs_per_launch_avg": a.mcs * a.steps / max(1, upd_launches),
+                "hbm_GBs_state_once_per_launch": 2 * state_bytes * upd_launches / upd_s / 1e9,
+                "hbm_peak_GBs": peak,
+                "update_share_of_step": upd_ms / ms if ms > 0 else None,
+                "updates_per_s_kernel_only": upd_total / upd_s}
+    else:
+        kname = {sca.KERNEL_FUSED: "k_fused_mcs", sca.KERNEL_WAVE: "k_wave",
+                 sca.KERNEL_TBLOCK: "k_tblock"}.get(kern, "k_half_step")
+        # bytes: the state read and written once per launch (one sublattice per two-pass
+        # launch; one MCS per fused launch; several per temporal-blocking launch)
+        alg_bytes = BYTES_PER_UPDATE * (L * L // 2 if kern == sca.KERNEL_TWO_PASS else L * L)
+        achieved = alg_bytes / avg_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(kname, L),
+                "kernel": kname, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_src == "measured" else peak_src,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+                "update_share_of_step": upd_ms / ms if ms > 0 else None,
+                "updates_per_s_kernel_only": upd_total / upd_s}
 
     # end-to-end through the C ABI with host buffers: pinned flat words in, state + W^2 out
     e2e = None
@@ -474,6 +520,7 @@ def run_ours(a, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         hms = e0.elapsed_time(e1)
         h_upd_ms, h_launches = half.timing_read()
+        h_kern = half.kernel_in_use()
         half.close()
         del half
         rate = L * L * n_half / (hms / 1000.0)
@@ -481,7 +528,10 @@ def run_ours(a, rank, world, local_rank):
                  "value": rate, "unit": UNIT,
                  "paper_titan_black_updates_per_s": 2.29e11,
                  "ratio_to_paper": rate / 2.29e11,
-                 "hbm_frac": BYTES_PER_UPDATE * L * L * n_half / (h_upd_ms / 1000.0) / 1e9 / peak}
+                 "kernel": h_kern, "launches": h_launches,
+                 # the canonical state read and written once per launch, over the launch time
+                 "hbm_frac_state_once_per_launch":
+                     BYTES_PER_UPDATE * L * L * h_launches / (h_upd_ms / 1000.0) / 1e9 / peak}
 
     batched = None
     if not a.no_batch and rank == 0 and world == 1 and (a.L, a.p, a.q) == (65536, 1.0, 0.0):

@@ -250,21 +250,34 @@ int sca_set_temporal_block(sca_sim *s, int mcs_per_launch)
 
 }  // extern "C"
 
-// Automatic kernel choice (measured on GB300): the fused kernel halves HBM traffic, which pays
-// once the state is far larger than L2 and the update is not arithmetic-bound; temporal
-// blocking (several MCS per launch in shared memory) wins while the lattice is small enough
-// that launches and L2 round trips dominate (dyadic draws up to L = 8192, per-site uniforms up
-// to L = 2048); the two-pass kernel covers the rest.
+// Automatic kernel choice (measured on GB300).  For a surface state the register-wavefront
+// kernel (4) wins wherever the lattice gives it enough tiles: with {0, 1} probabilities from
+// L = 4096 on (8 MCS per launch up to L = 8192, 16 above), with dyadic draws from L = 65536 on
+// (2 MCS per launch; below that the fused kernel's HBM-bound pass is as fast).  Otherwise the
+// fused kernel halves HBM traffic once the state is far larger than L2 and the update is not
+// arithmetic-bound; shared-memory temporal blocking (several MCS per launch) wins while the
+// lattice is small enough that launches and L2 round trips dominate (dyadic draws up to
+// L = 8192, per-site uniforms up to L = 2048); the two-pass kernel covers the rest.
+static uint32_t wave_default_k(uint32_t L, int mode)
+{
+    return mode == 0 ? (L >= 16384 ? 16u : 8u) : 2u;
+}
+
 int sca::effective_kernel(const sca_sim *s, int *tb_k)
 {
     int k = s->kernel;
     int kk = s->tb_k;
-    if (k == 4) kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : (uint32_t)wave_max_k((int)s->R.mode),
-                                      (int)s->R.mode);
+    const int mode = (int)s->R.mode;
+    if (k == 4) kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : wave_default_k(s->L, mode), mode);
     if (k == 0) {
         uint32_t ns;
         size_t sm;
-        if (fused_supported(s->L) && s->L >= 32768 && s->R.mode != 2) {
+        const bool wave_ok = s->surface && ((mode == 0 && s->L >= 4096) || (mode == 1 && s->L >= 65536)) &&
+                             wave_supported(s->L, wave_default_k(s->L, mode), mode);
+        if (wave_ok) {
+            k = 4;
+            kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : wave_default_k(s->L, mode), mode);
+        } else if (fused_supported(s->L) && s->L >= 32768 && s->R.mode != 2) {
             k = 2;
         } else if (s->R.mode != 2 && s->L <= 8192 && tblock_plan(s->L, s->tb_set ? kk : 8, &ns, &sm)) {
             k = 3;

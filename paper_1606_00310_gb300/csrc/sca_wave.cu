@@ -5,9 +5,13 @@
 
 namespace sca {
 
-// Dyadic instantiations (other translation unit, compiled in parallel).
-cudaError_t launch_wave_dyadic(const WaveArgs &a, int K, int grid, cudaStream_t st);
-int wave_dyadic_blocks_per_sm(int K);
+// Dyadic instantiations (other translation unit, compiled in parallel); V words per lane.
+cudaError_t launch_wave_dyadic(const WaveArgs &a, int K, int V, int grid, cudaStream_t st);
+int wave_dyadic_blocks_per_sm(int K, int V);
+
+// Words per lane: dyadic draws take four (one Philox call per draw for the four words) when
+// the row length allows, else one; {0, 1} probabilities one.
+static int wave_V(uint32_t L, int mode) { return mode == 1 && (L / 64) % 4 == 0 ? 4 : 1; }
 
 template <int K, bool DP, bool DQ>
 static int blocks_per_sm()
@@ -15,7 +19,7 @@ static int blocks_per_sm()
     static int n = 0;
     if (n == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wave<K, 0, DP, DQ>, 32 * kWaveWarps, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wave<K, 1, kWaveU0, 0, DP, DQ>, 32 * kWaveWarps, 0) !=
                 cudaSuccess || b <= 0)
             b = 1;
         n = b;
@@ -36,10 +40,10 @@ template <int K>
 static cudaError_t launch_mode0(const WaveArgs &a, int grid, cudaStream_t st)
 {
     const bool dp = a.R.Pp != 0, dq = a.R.Pq != 0;
-    if (dp && dq) k_wave<K, 0, true, true><<<grid, 32 * kWaveWarps, 0, st>>>(a);
-    else if (dp) k_wave<K, 0, true, false><<<grid, 32 * kWaveWarps, 0, st>>>(a);
-    else if (dq) k_wave<K, 0, false, true><<<grid, 32 * kWaveWarps, 0, st>>>(a);
-    else k_wave<K, 0, false, false><<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    if (dp && dq) k_wave<K, 1, kWaveU0, 0, true, true><<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else if (dp) k_wave<K, 1, kWaveU0, 0, true, false><<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else if (dq) k_wave<K, 1, kWaveU0, 0, false, true><<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else k_wave<K, 1, kWaveU0, 0, false, false><<<grid, 32 * kWaveWarps, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -53,9 +57,9 @@ uint32_t wave_pick_k(uint32_t want, int mode)
     return cap ? k : 0;
 }
 
-static int blocks_for(int K, const Rule &R)
+static int blocks_for(int K, int V, const Rule &R)
 {
-    if (R.mode == 1) return wave_dyadic_blocks_per_sm(K);
+    if (R.mode == 1) return wave_dyadic_blocks_per_sm(K, V);
     const bool dp = R.Pp != 0, dq = R.Pq != 0;
     switch (K) {
     case 1: return blocks_mode0<1>(dp, dq);
@@ -73,12 +77,12 @@ static bool wave_plan(uint32_t L, uint32_t k, int mode, uint32_t bands, int bloc
 {
     if (L < 64 || L % 64 != 0 || k == 0 || (k & (k - 1)) != 0) return false;
     if ((int)k > wave_max_k(mode)) return false;
-    const uint32_t W = L / 64;
-    const uint32_t nc = (W + kWaveTileWords - 1) / kWaveTileWords;
+    const uint32_t W = L / 64, tw = kWaveTileWords * (uint32_t)wave_V(L, mode);
+    const uint32_t nc = (W + tw - 1) / tw;
     uint32_t nb = bands;
     if (nb == 0) {
         const uint64_t warps = (uint64_t)sm_count() * blocks_per_sm * kWaveWarps;
-        nb = (uint32_t)((warps + nc / 2) / nc);
+        nb = (uint32_t)(warps / nc);            // every tile resident at once: no tail wave
         const uint32_t cap = L / (8u * k);
         if (nb > cap) nb = cap;
         if (nb == 0) nb = 1;
@@ -101,12 +105,13 @@ cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t
     const int mode = (int)R.mode;
     uint32_t nb, nc;
     if (!wave_plan(L, k, mode, bands, 1, &nb, &nc)) return cudaErrorInvalidValue;
-    if (!wave_plan(L, k, mode, bands, blocks_for((int)k, R), &nb, &nc)) return cudaErrorInvalidValue;
+    const int V = wave_V(L, mode);
+    if (!wave_plan(L, k, mode, bands, blocks_for((int)k, V, R), &nb, &nc)) return cudaErrorInvalidValue;
     const WaveArgs a{src, dst, L, L / 64, nb, nc, t0, t_dev, R};
     const uint64_t tiles = (uint64_t)nb * nc;
     const int grid = (int)((tiles + kWaveWarps - 1) / kWaveWarps);
     count_launches(1);
-    if (mode == 1) return launch_wave_dyadic(a, (int)k, grid, st);
+    if (mode == 1) return launch_wave_dyadic(a, (int)k, V, grid, st);
     switch (k) {
     case 1: return launch_mode0<1>(a, grid, st);
     case 2: return launch_mode0<2>(a, grid, st);

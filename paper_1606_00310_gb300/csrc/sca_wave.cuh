@@ -42,8 +42,18 @@ struct WaveArgs {
 };
 
 constexpr int kWaveWarps = 4;          // warps (independent tiles) per CTA
-constexpr int kWaveRaw = 3;            // rows of sy- words loaded ahead of the wavefront
 constexpr uint32_t kWaveTileWords = 30; // words a warp tile owns (32 lanes minus two halos)
+// Rows per loop iteration (even): larger blocks shift the row window less often, smaller ones
+// keep the unrolled loop inside the instruction cache; the dyadic update carries a Philox
+// call per half-step, so it takes the smaller block.
+#ifndef SCA_WAVE_U0
+#define SCA_WAVE_U0 4
+#endif
+#ifndef SCA_WAVE_U1
+#define SCA_WAVE_U1 2
+#endif
+constexpr int kWaveU0 = SCA_WAVE_U0;   // {0, 1} probabilities
+constexpr int kWaveU1 = SCA_WAVE_U1;   // dyadic draws
 
 __device__ __forceinline__ uint32_t wave_xor_prefix(uint32_t g)
 {
@@ -55,14 +65,77 @@ __device__ __forceinline__ uint32_t wave_xor_prefix(uint32_t g)
     return g;
 }
 
-// MODE 0: p, q in {0, 1} with DP = (p == 1), DQ = (q == 1); MODE 1: dyadic draws.
-template <int K, int MODE, bool DP, bool DQ>
+template <int V>
+__device__ __forceinline__ void wave_ld(const uint32_t *p, uint32_t (&r)[V])
+{
+    if constexpr (V == 4) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+        r[0] = q.x; r[1 % V] = q.y; r[2 % V] = q.z; r[3 % V] = q.w;
+    } else if constexpr (V == 2) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+        r[0] = q.x; r[1 % V] = q.y;
+    } else {
+        r[0] = __ldg(p);
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void wave_st(uint32_t *p, const uint32_t (&r)[V])
+{
+    if constexpr (V == 4) *reinterpret_cast<uint4 *>(p) = make_uint4(r[0], r[1 % V], r[2 % V], r[3 % V]);
+    else if constexpr (V == 2) *reinterpret_cast<uint2 *>(p) = make_uint2(r[0], r[1 % V]);
+    else *p = r[0];
+}
+
+// Dyadic xi words (Sec. III construction, as xi_dyadic) for V words starting at word unit u0,
+// where u0 is a multiple of 4 when V == 4 (one Philox call per draw gives all four words).
+template <int V>
+__device__ __forceinline__ void wave_xi(const Rule &R, uint64_t u0, uint64_t t, int s, uint32_t (&xp)[V],
+                                        uint32_t (&xq)[V])
+{
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        xp[v] = (R.np == 0 && R.Pp) ? 0xFFFFFFFFu : 0u;
+        xq[v] = (R.nq == 0 && R.Pq) ? 0xFFFFFFFFu : 0u;
+    }
+#pragma unroll 1
+    for (int i = (int)R.n_draws; i >= 1; --i) {
+        uint32_t r[V];
+        if constexpr (V == 4) {
+            const Ctr4 o = philox4x32_10_rk(draw_counter(u0 >> 2, t, s, i, 0), R.rk);
+            r[0] = o.x; r[1 % V] = o.y; r[2 % V] = o.z; r[3 % V] = o.w;
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const uint64_t u = u0 + v;
+                r[v] = lane_of(philox4x32_10_rk(draw_counter(u >> 2, t, s, i, 0), R.rk), (uint32_t)(u & 3));
+            }
+        }
+        if (i <= (int)R.np) {
+            const bool first = (i == (int)R.np);
+            const bool bit = (R.Pp >> (R.np - i)) & 1u;
+#pragma unroll
+            for (int v = 0; v < V; ++v) xp[v] = first ? r[v] : (bit ? (r[v] | xp[v]) : (r[v] & xp[v]));
+        }
+        if (i <= (int)R.nq) {
+            const bool first = (i == (int)R.nq);
+            const bool bit = (R.Pq >> (R.nq - i)) & 1u;
+#pragma unroll
+            for (int v = 0; v < V; ++v) xq[v] = first ? r[v] : (bit ? (r[v] | xq[v]) : (r[v] & xq[v]));
+        }
+    }
+}
+
+// V consecutive words per lane (V = 1, 2 or 4; the lattice's words per row must be a multiple
+// of V).  U rows per loop iteration: the loop body holds U x 2K half-step updates, and the row
+// window (2K+1+U slots) shifts by U slots per iteration.  MODE 0: p, q in {0, 1} with
+// DP = (p == 1), DQ = (q == 1); MODE 1: dyadic draws.
+template <int K, int V, int U, int MODE, bool DP, bool DQ>
 __global__ void __launch_bounds__(32 * kWaveWarps) k_wave(const WaveArgs a)
 {
-    constexpr int S = 2 * K;                                // half-steps per launch
-    constexpr int NH = ((S + 2 + 2 * kWaveRaw - 1) / (2 * kWaveRaw)) * (2 * kWaveRaw);  // rows of height bits
-    constexpr int NRAW = kWaveRaw;
-    static_assert(NH % 2 == 0 && NH % NRAW == 0 && NH >= S + 2, "window");
+    constexpr int S = 2 * K;                    // half-steps per launch
+    constexpr int NW = S + 1 + U;               // row slots: slot of row R = R - R0 + S + 1
+    static_assert(U % 2 == 0, "U rows per iteration keeps the row parity of each slot");
     const uint32_t FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const uint32_t tile = blockIdx.x * kWaveWarps + threadIdx.x / 32;
@@ -82,119 +155,174 @@ __global__ void __launch_bounds__(32 * kWaveWarps) k_wave(const WaveArgs a)
     uint32_t *DX0 = a.dst, *DY0 = a.dst + plane, *DX1 = a.dst + 2 * plane, *DY1 = a.dst + 3 * plane;
     const uint64_t t0 = a.t_dev ? *a.t_dev + a.t0 : a.t0;
 
-    const int64_t jj = (int64_t)col * kWaveTileWords - 1 + lane;
+    // lane l owns words jj .. jj + V - 1 of every row; lanes 0 and 31 are halo
+    const int64_t jj = (int64_t)col * (kWaveTileWords * V) - V + (int64_t)lane * V;
     const uint32_t j = (uint32_t)(((jj % (int64_t)W) + W) % (int64_t)W);
     const bool own = lane >= 1 && lane <= 30 && jj < (int64_t)W;
 
-    uint32_t h[NH][2];              // height bits, row slot = band row mod NH, [sublattice]
-    uint32_t raw[NRAW][2];          // sy- words of rows loaded ahead, slot = band row mod NRAW
+    uint32_t h[NW][2][V];           // height bits [slot][sublattice][word]
+    uint32_t rc[U][2][V], rn[U][2][V];   // sy- words of this block's rows / the next block's
 #pragma unroll
-    for (int i = 0; i < NH; ++i) h[i][0] = h[i][1] = 0u;
+    for (int i = 0; i < NW; ++i)
+#pragma unroll
+        for (int v = 0; v < V; ++v) h[i][0][v] = h[i][1][v] = 0u;
 
     // First row (even lattice row: sublattice 0 at even x): integrate along x.  With e(x) =
     // b(x) xor b(x-1) = sx-bit(x) xor (x & 1), the even-x bits obey b_e(k) = b_e(k-1) xor
-    // ~sx1(k-1) xor sx0(k); the prefix xor runs over the whole warp (lane 0's reference bit is
-    // arbitrary: flipping every bit of a connected region changes no slope).
+    // ~sx1(k-1) xor sx0(k); the prefix xor runs over the lane's words and then the warp (lane
+    // 0's reference bit is arbitrary: flipping every bit of a connected region changes no slope).
     {
         const size_t o = (size_t)first * W + j;
-        const uint32_t sx0 = __ldg(SX0 + o), nsx1 = ~__ldg(SX1 + o);
-        const uint32_t prev = __shfl_up_sync(FULL, nsx1, 1);
-        uint32_t pre = wave_xor_prefix(sx0 ^ __funnelshift_l(prev, nsx1, 1));
-        uint32_t par = pre >> 31, incl = par;
+        uint32_t sx0[V], nsx1[V];
+        wave_ld<V>(SX0 + o, sx0);
+        wave_ld<V>(SX1 + o, nsx1);
+#pragma unroll
+        for (int v = 0; v < V; ++v) nsx1[v] = ~nsx1[v];
+        const uint32_t prev = __shfl_up_sync(FULL, nsx1[V - 1], 1);
+        uint32_t pre[V], c = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            pre[v] = wave_xor_prefix(sx0[v] ^ __funnelshift_l(v ? nsx1[(v + V - 1) % V] : prev, nsx1[v], 1));
+            pre[v] ^= 0u - c;
+            c = pre[v] >> 31;
+        }
+        uint32_t incl = c;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t t = __shfl_up_sync(FULL, incl, d);
             if (lane >= d) incl ^= t;
         }
-        pre ^= 0u - (incl ^ par);
-        h[0][0] = pre;
-        h[0][1] = pre ^ nsx1;
+        const uint32_t flip = 0u - (incl ^ c);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            h[S + 1][0][v] = pre[v] ^ flip;
+            h[S + 1][1][v] = pre[v] ^ flip ^ nsx1[v];
+        }
     }
     uint32_t yl = first + 1 >= L ? first + 1 - L : first + 1;     // next row to load
 #pragma unroll
-    for (int d = 1; d <= NRAW; ++d) {
-        if ((uint32_t)d < NR) {
-            raw[d % NRAW][0] = __ldg(SY0 + (size_t)yl * W + j);
-            raw[d % NRAW][1] = __ldg(SY1 + (size_t)yl * W + j);
+    for (int u = 1; u < U; ++u) {
+        if ((uint32_t)u < NR) {
+            wave_ld<V>(SY0 + (size_t)yl * W + j, rc[u][0]);
+            wave_ld<V>(SY1 + (size_t)yl * W + j, rc[u][1]);
         }
         if (++yl == L) yl = 0;
     }
     uint32_t yu = first;                                          // lattice row of row R
 
-    for (uint32_t R0 = 0; R0 < NR; R0 += NH) {
+    for (uint32_t R0 = 0; R0 < NR; R0 += U) {
+        // sy- words of the next block's rows, in flight while this block computes
 #pragma unroll
-        for (int u = 0; u < NH; ++u) {
+        for (int u = 0; u < U; ++u) {
+            if (R0 + U + u < NR) {
+                wave_ld<V>(SY0 + (size_t)yl * W + j, rn[u][0]);
+                wave_ld<V>(SY1 + (size_t)yl * W + j, rn[u][1]);
+            }
+            if (++yl == L) yl = 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
             const uint32_t R = R0 + (uint32_t)u;
             if (R >= NR) break;
+            constexpr int base = S + 1;             // slot of row R0
             if (R > 0) {
                 // b(x, y) = b(x, y-1) xor sy-bit(x, y) xor s (sites of sublattice s have parity s)
-                uint32_t(&hr)[2] = h[u];
-                const uint32_t(&hp)[2] = h[(u + NH - 1) % NH];
-                hr[0] = hp[1] ^ raw[u % NRAW][0];
-                hr[1] = ~(hp[0] ^ raw[u % NRAW][1]);
-                if (R + NRAW < NR) {
-                    raw[u % NRAW][0] = __ldg(SY0 + (size_t)yl * W + j);
-                    raw[u % NRAW][1] = __ldg(SY1 + (size_t)yl * W + j);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    h[base + u][0][v] = h[base + u - 1][1][v] ^ rc[u][0][v];
+                    h[base + u][1][v] = ~(h[base + u - 1][0][v] ^ rc[u][1][v]);
                 }
-                if (++yl == L) yl = 0;
             }
             // rows of sublattice s at parity (s + y) & 1 == 1 sit one site right; for every
-            // half-step of this position (s + y) & 1 == (R + 1) & 1
+            // half-step of this position (s + y) & 1 == (R + 1) & 1, and R0 is even
             const bool right_shift = ((u + 1) & 1) != 0;
 #pragma unroll
             for (int i = 1; i <= S; ++i) {
                 const int s = (i - 1) & 1, ns = s ^ 1;
-                uint32_t &b = h[(u - i + 2 * NH) % NH][s];
-                const uint32_t up = h[(u - i - 1 + 2 * NH) % NH][ns];
-                const uint32_t dn = h[(u - i + 1 + 2 * NH) % NH][ns];
-                const uint32_t mid = h[(u - i + 2 * NH) % NH][ns];
-                uint32_t side;
-                if (right_shift) side = __funnelshift_r(mid, __shfl_down_sync(FULL, mid, 1), 1);
-                else side = __funnelshift_l(__shfl_up_sync(FULL, mid, 1), mid, 1);
-                // e(n) = b xor b(n) for the four neighbours
-                const uint32_t e_or = (b ^ up) | (b ^ dn) | (b ^ mid) | (b ^ side);
-                const uint32_t e_and = (b ^ up) & (b ^ dn) & (b ^ mid) & (b ^ side);
-                // local minimum: every e == s; local maximum: every e == 1 - s
-                const uint32_t is_min = s == 0 ? ~e_or : e_and;
-                const uint32_t is_max = s == 0 ? e_and : ~e_or;
-                uint32_t m;
-                if constexpr (MODE == 0) {
-                    m = (DP ? is_min : 0u) | (DQ ? is_max : 0u);
+                const int c = base + u - i;         // slot of row R - i
+                uint32_t(&b)[V] = h[c][s];
+                const uint32_t(&up)[V] = h[c - 1][ns];
+                const uint32_t(&dn)[V] = h[c + 1][ns];
+                const uint32_t(&mid)[V] = h[c][ns];
+                // the x-neighbour that is not in the same bit position: bit k+1 of the other
+                // sublattice when this row sits right, else bit k-1
+                uint32_t side[V];
+                if (right_shift) {
+                    const uint32_t nx = __shfl_down_sync(FULL, mid[0], 1);
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        side[v] = __funnelshift_r(mid[v], v + 1 < V ? mid[(v + 1) % V] : nx, 1);
                 } else {
-                    const uint32_t y = (yu + 2 * L - (uint32_t)i) % L;
-                    uint32_t xp[1], xq[1];
-                    xi_dyadic<1>(a.R, a.R.rk, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
-                    m = (xp[0] & is_min) | (xq[0] & is_max);
+                    const uint32_t pv = __shfl_up_sync(FULL, mid[V - 1], 1);
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        side[v] = __funnelshift_l(v ? mid[(v + V - 1) % V] : pv, mid[v], 1);
                 }
-                b ^= m;
+                uint32_t xp[V], xq[V];
+                if constexpr (MODE == 1) {
+                    const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
+                    wave_xi<V>(a.R, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    // e(n) = b xor b(n) for the four neighbours; local minimum: every e == s,
+                    // local maximum: every e == 1 - s
+                    const uint32_t e_or = (b[v] ^ up[v]) | (b[v] ^ dn[v]) | (b[v] ^ mid[v]) | (b[v] ^ side[v]);
+                    const uint32_t e_and = (b[v] ^ up[v]) & (b[v] ^ dn[v]) & (b[v] ^ mid[v]) & (b[v] ^ side[v]);
+                    const uint32_t is_min = s == 0 ? ~e_or : e_and;
+                    const uint32_t is_max = s == 0 ? e_and : ~e_or;
+                    uint32_t m;
+                    if constexpr (MODE == 0) m = (DP ? is_min : 0u) | (DQ ? is_max : 0u);
+                    else m = (xp[v] & is_min) | (xq[v] & is_max);
+                    b[v] ^= m;
+                }
             }
-            if (R >= 4u * K + 2u) {                 // band row R - 2K (lattice row y) is final
-                const uint32_t(&hr)[2] = h[(u - S + 2 * NH) % NH];
-                const uint32_t(&hp)[2] = h[(u - S - 1 + 2 * NH) % NH];
+            if (R >= 4u * K + 2u) {                 // row R - 2K (lattice row y) is final
+                const uint32_t(&hr)[2][V] = h[base + u - S];
+                const uint32_t(&hp)[2][V] = h[base + u - S - 1];
                 const uint32_t y = y0 + R - 4u * K - 2u;
                 // sy-bit = b xor b(x, y-1) xor s and sx-bit = b xor b(x-1, y) xor s.  In even
                 // rows sublattice 0 sits at even x, so its left neighbour is bit k-1 of the
                 // sublattice-1 word and sublattice 1's is bit k of the sublattice-0 word; odd
                 // rows the other way round (y has the parity of u).
-                const uint32_t sy0 = hr[0] ^ hp[1], sy1 = ~(hr[1] ^ hp[0]);
-                uint32_t sx0, sx1;
-                if ((u & 1) == 0) {
-                    sx0 = hr[0] ^ __funnelshift_l(__shfl_up_sync(FULL, hr[1], 1), hr[1], 1);
-                    sx1 = ~(hr[1] ^ hr[0]);
-                } else {
-                    sx0 = hr[0] ^ hr[1];
-                    sx1 = ~(hr[1] ^ __funnelshift_l(__shfl_up_sync(FULL, hr[0], 1), hr[0], 1));
+                const int lo = (u & 1) ? 1 : 0;             // sublattice whose left neighbour is shifted
+                const uint32_t pv = __shfl_up_sync(FULL, hr[lo ^ 1][V - 1], 1);
+                uint32_t sx[2][V], sy[2][V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    sy[0][v] = hr[0][v] ^ hp[1][v];
+                    sy[1][v] = ~(hr[1][v] ^ hp[0][v]);
+                    const uint32_t left = __funnelshift_l(v ? hr[lo ^ 1][(v + V - 1) % V] : pv, hr[lo ^ 1][v], 1);
+                    sx[lo][v] = hr[lo][v] ^ left;
+                    sx[lo ^ 1][v] = hr[lo ^ 1][v] ^ hr[lo][v];
                 }
+#pragma unroll
+                for (int v = 0; v < V; ++v) sx[1][v] = ~sx[1][v];
                 if (own) {
                     const size_t o = (size_t)y * W + j;
-                    DX0[o] = sx0;
-                    DY0[o] = sy0;
-                    DX1[o] = sx1;
-                    DY1[o] = sy1;
+                    wave_st<V>(DX0 + o, sx[0]);
+                    wave_st<V>(DY0 + o, sy[0]);
+                    wave_st<V>(DX1 + o, sx[1]);
+                    wave_st<V>(DY1 + o, sy[1]);
                 }
             }
             if (++yu == L) yu = 0;
         }
+        // slide the window by U rows
+#pragma unroll
+        for (int c = 0; c <= S; ++c)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                h[c][0][v] = h[c + U][0][v];
+                h[c][1][v] = h[c + U][1][v];
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                rc[u][0][v] = rn[u][0][v];
+                rc[u][1][v] = rn[u][1][v];
+            }
     }
 }
 

@@ -112,3 +112,36 @@ def test_wave_rejects_what_it_cannot_run(sca):
             sim.set_wave_bands(-1)
         with pytest.raises(sca.ScaError):
             sim.set_wave_bands(129)
+
+
+def test_wave_resumes_from_a_set_state(sca):
+    """A surface loaded with set_state (evolved by the oracle) passes the surface check and
+    kernel 4 continues it exactly as the oracle does."""
+    L, seed, p, q = 512, 6, 0.75, 0.25
+    bx, by = o.init_flat(L)
+    o.run(bx, by, seed, p, q, t0=0, n_mcs=5)
+    start = o.pack(bx, by)
+    o.run(bx, by, seed, p, q, t0=5, n_mcs=7)
+    with sca.Sim(L, seed=seed, p=p, q=q, kernel=sca.KERNEL_WAVE) as sim:
+        sim.set_state(start, t=5)
+        sim.step(7)
+        assert np.array_equal(sim.get_state(), o.pack(bx, by))
+
+
+def test_wave_refuses_a_state_that_is_not_a_surface(sca):
+    """One flipped slope bit breaks two plaquettes: kernel 4 reports SCA_ESTATE instead of
+    evolving it, while the slope-based kernels still accept the words as they are."""
+    L = 256
+    bx, by = o.init_flat(L)
+    words = o.pack(bx, by)
+    words[5] ^= 1 << 7
+    with sca.Sim(L, seed=1, p=0.75, q=0.25, kernel=sca.KERNEL_WAVE) as sim:
+        sim.set_state(words)
+        with pytest.raises(sca.ScaError) as ei:
+            sim.step(1)
+        assert ei.value.code == sca.ESTATE
+        sim.set_kernel(sca.KERNEL_TWO_PASS)
+        sim.step(1)
+        sim.reset()                       # a reset state is a surface again
+        sim.set_kernel(sca.KERNEL_WAVE)
+        sim.step(2)
