@@ -4,7 +4,8 @@
 Workload (one "step"): an L = 65536 periodic lattice (4.3 G sites, 1 GiB of packed slopes),
 flat start, p = 1, q = 0, 1024 Monte-Carlo steps with the exact roughness W^2 observed at
 MCS 1, 2, 4, ..., 1024.  Metric: site updates per second (L^2 attempts per MCS).  The state
-(1 GiB, read and written every MCS) is far larger than L2, so no flush is needed between steps.
+(1 GiB, read and written at least once per update launch, i.e. every MCS or every 16 MCS
+depending on the kernel) is far larger than L2, so no flush is needed between steps.
 
 Arms:
   default          the CUDA library through its C ABI, state resident in HBM;
@@ -52,7 +53,9 @@ def parse():
     ap.add_argument("--p", type=float, default=1.0)
     ap.add_argument("--q", type=float, default=0.0)
     ap.add_argument("--mcs", type=int, default=1024)
-    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 two-pass, 2 fused")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="0 auto, 1 two-pass, 2 fused, 3 shared-memory temporal blocking, "
+                         "4 register wavefront on height bits")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the p=1/2 context line")

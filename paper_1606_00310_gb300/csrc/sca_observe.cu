@@ -4,83 +4,35 @@
 // the definition used here: h(0,0) = 0, h(0,y) = sum of sy-(0,y') for y' = 1..y, and
 // h(x,y) = h(0,y) + sum of sx-(x',y) for x' = 1..x (slopes as +-1).  S1 = sum h,
 // S2 = sum h^2 (128-bit), num = N * S2 - S1^2 (128-bit); W^2 = num / N^2.  Heights are never
-// stored: one kernel scans column 0, one kernel scans every row in registers (popcounts of
-// the interleaved even-x / odd-x words give each thread's offset) and reduces per block,
-// and a last kernel combines the block partials in 128-bit integers.
+// stored.  With g(x,y) = h(x,y) - h(0,y), every row y reduces to A_y = sum_x g and
+// B_y = sum_x g^2 on its own, and
+//   S1 = sum_y (L h(0,y) + A_y),   S2 = sum_y (L h(0,y)^2 + 2 h(0,y) A_y + B_y),
+// so one kernel reduces every row independently (a warp per row: each lane walks a contiguous
+// chunk of words with a table over 8 sites at a time, a warp scan of the chunk totals places
+// the chunks) and writes A_y with the row's column-0 slope bit, and a second kernel integrates
+// column 0 and combines everything in 128-bit integers.
 #include "sca_internal.h"
 
 namespace sca {
 
-__device__ __forceinline__ int64_t warp_incl_scan(int64_t v, int width)
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v)
 {
     const int lane = threadIdx.x & 31;
-    for (int o = 1; o < width; o <<= 1) {
-        const int64_t u = __shfl_up_sync(0xFFFFFFFFu, v, o, width);
-        if ((lane & (width - 1)) >= o) v += u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += u;
     }
     return v;
 }
 
-// Column 0: site (0, y) is site k = 0 of sublattice y & 1, so sy-(0,y) is bit 0 of word 0 of
-// row y in plane (y & 1, y).  One block of 1024 threads; each thread scans a run of rows.
-__global__ void __launch_bounds__(1024) k_obs_col0(const uint32_t *A, uint32_t L, int64_t *h0,
-                                                   ObsPartial *col_flag)
+__device__ __forceinline__ int64_t warp_sum(int64_t v)
 {
-    __shared__ int64_t warp_tot[32];
-    const uint32_t W = L / 64;
-    const size_t plane = (size_t)L * W;
-    const uint32_t per = (L + blockDim.x - 1) / blockDim.x;
-    const uint32_t y0 = threadIdx.x * per;
-    auto sy0 = [&](uint32_t y) -> int64_t {
-        const uint32_t s = y & 1u;
-        return 2 * (int64_t)(A[(size_t)(s * 2 + 1) * plane + (size_t)y * W] & 1u) - 1;
-    };
-    int64_t local = 0;
-    // the rows of one thread are independent loads: issue them in batches so their latencies
-    // overlap instead of adding up
-    for (uint32_t yb = y0; yb < y0 + per && yb < L; yb += 8) {
-        int64_t v[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t y = yb + k;
-            v[k] = (y < y0 + per && y < L && y > 0) ? sy0(y) : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) local += v[k];
-    }
-    int64_t incl = warp_incl_scan(local, 32);
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 31) warp_tot[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        int64_t v = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
-        v = warp_incl_scan(v, 32);
-        warp_tot[lane] = v;
-    }
-    __syncthreads();
-    int64_t run = incl - local + (wid > 0 ? warp_tot[wid - 1] : 0);
-    for (uint32_t y = y0; y < y0 + per && y < L; ++y) {
-        if (y > 0) run += sy0(y);
-        h0[y] = run;
-    }
-    if (threadIdx.x == blockDim.x - 1) {
-        // closure around the y cycle: h(0, L-1) + sy-(0, 0) must return to h(0, 0) = 0
-        const int64_t total = warp_tot[(blockDim.x >> 5) - 1];
-        col_flag->flags = (total + sy0(0) != 0) ? 1u : 0u;
-    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
 }
 
-struct RowsArgs {
-    const uint32_t *A;
-    uint32_t L, W;
-    int T, TP;
-    const int64_t *h0;
-    ObsPartial *part;
-};
-
-// Rows: a team of threads spans row y; thread `lane` owns words j = lane*V .. lane*V+V-1 of
-// the even-x plane (sublattice y & 1) and the odd-x plane (sublattice (y & 1) ^ 1), i.e.
-// x in [64 j, 64 (j + V)).
 // Table over the 256 values of (4 even-x bits, 4 odd-x bits): for the 8 sites in x order
 // (e0, o0, e1, o1, ...), slopes s = 2b - 1, running offsets d_k = s_0 + ... + s_k:
 // bits 0-4: sum s + 8, bits 5-11: sum d + 36, bits 12-19: sum d^2.
@@ -98,164 +50,229 @@ __device__ __forceinline__ uint32_t nibble_pair_entry(uint32_t i)
     return (uint32_t)(d + 8) | ((uint32_t)(sd + 36) << 5) | ((uint32_t)sd2 << 12);
 }
 
-template <int V>
-__global__ void __launch_bounds__(1024) k_obs_rows(const RowsArgs a)
+// 32 sites of the even-x word e and the odd-x word o (x order e0, o0, e1, o1, ...), appended
+// to a chunk whose running offset is d: sd += sum of offsets, sd2 += sum of squared offsets.
+// A block of 8 sites with table entry (S, A, B) after offset D adds 8D + A, 8D^2 + 2DA + B.
+// tab: the table replicated per lane, entry i of lane l at tab[32 i + l], so the 32 lanes of a
+// warp always read 32 different banks.
+__device__ __forceinline__ void obs_word_pair(const uint32_t *tab, uint32_t e, uint32_t o, int32_t &d,
+                                              int32_t &sd, int64_t &sd2)
 {
-    __shared__ uint32_t tab[256];
-    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) tab[i] = nibble_pair_entry(i);
-    __shared__ int64_t warp_tot[32];
-    __shared__ int64_t red1[32];
-    __shared__ unsigned long long red2[32][2];
-    __shared__ uint32_t red_flag;
-    const int tpb = blockDim.x / a.TP;
-    const int team = threadIdx.x / a.TP;
-    const int lane = threadIdx.x - team * a.TP;
-    const int wid = threadIdx.x >> 5, wl = threadIdx.x & 31;
-    const bool owner = lane < a.T;
-    const uint32_t L = a.L, W = a.W;
-    const size_t plane = (size_t)L * W;
-    if (threadIdx.x == 0) red_flag = 0;
-    __syncthreads();
-
-    int64_t s1 = 0;
-    unsigned __int128 s2 = 0;
-    uint32_t flags = 0;
-    for (uint32_t base = blockIdx.x * tpb; base < L; base += gridDim.x * tpb) {
-        const uint32_t y = base + team;
-        const bool active = owner && y < L;
-        const uint32_t j = (uint32_t)lane * V;
-        uint32_t e[V], o[V];
-        int64_t csum = 0;
-        if (active) {
-            const uint32_t se = y & 1u, so = se ^ 1u;
-            const uint32_t *pe = a.A + (size_t)(se * 2) * plane + (size_t)y * W + j;
-            const uint32_t *po = a.A + (size_t)(so * 2) * plane + (size_t)y * W + j;
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                e[v] = pe[v];
-                o[v] = po[v];
-                csum += 2 * (__popc(e[v]) + __popc(o[v])) - 64;
-            }
-        }
-        // exclusive prefix of csum over the team, and the team total
-        int64_t excl, total;
-        if (a.TP <= 32) {
-            const int64_t incl = warp_incl_scan(csum, a.TP);
-            excl = incl - csum;
-            total = __shfl_sync(0xFFFFFFFFu, incl, (wl & ~(a.TP - 1)) + a.TP - 1);
-        } else {
-            const int64_t incl = warp_incl_scan(csum, 32);
-            if (wl == 31) warp_tot[wid] = incl;
-            __syncthreads();
-            const int w0 = (team * a.TP) >> 5;
-            const int nw = a.TP >> 5;
-            int64_t before = 0, all = 0;
-            for (int w = 0; w < nw; ++w) {
-                if (w0 + w < wid) before += warp_tot[w0 + w];
-                all += warp_tot[w0 + w];
-            }
-            __syncthreads();
-            excl = before + incl - csum;
-            total = all;
-        }
-        if (active) {
-            if (lane == 0 && total != 0) flags |= 2u;   // row does not close around x
-            const int64_t s0 = 2 * (int64_t)(a.A[(size_t)((y & 1u) * 2) * plane + (size_t)y * W] & 1u) - 1;
-            const int64_t H = a.h0[y] + excl - s0;      // h(x) = H + d(x), d summed from x0
-            // 8 sites at a time: with D the offset before a block and (S, A, B) its table entry,
-            // the block adds 8D + A to sum d, 8D^2 + 2DA + B to sum d^2, and S to D
-            int32_t d = 0, sd = 0, sd2 = 0;
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t ent = tab[((e[v] >> (4 * k)) & 0xFu) | (((o[v] >> (4 * k)) & 0xFu) << 4)];
-                    const int32_t S = (int32_t)(ent & 31u) - 8;
-                    const int32_t A = (int32_t)((ent >> 5) & 127u) - 36;
-                    const int32_t B = (int32_t)(ent >> 12);
-                    sd += 8 * d + A;
-                    sd2 += 8 * d * d + 2 * d * A + B;
-                    d += S;
-                }
-            }
-            const int64_t n = 64 * V;
-            s1 += n * H + sd;
-            s2 += (unsigned __int128)(uint64_t)(n * H * H + 2 * H * (int64_t)sd + (int64_t)sd2);
-        }
-    }
-    // block reduction
-    for (int off = 16; off > 0; off >>= 1) {
-        s1 += __shfl_down_sync(0xFFFFFFFFu, s1, off);
-        const uint64_t lo = (uint64_t)s2, hi = (uint64_t)(s2 >> 64);
-        const uint64_t olo = __shfl_down_sync(0xFFFFFFFFu, lo, off);
-        const uint64_t ohi = __shfl_down_sync(0xFFFFFFFFu, hi, off);
-        s2 += ((unsigned __int128)ohi << 64) | olo;
-    }
-    if (flags) atomicOr(&red_flag, flags);
-    if (wl == 0) {
-        red1[wid] = s1;
-        red2[wid][0] = (uint64_t)s2;
-        red2[wid][1] = (uint64_t)(s2 >> 64);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t t1 = 0;
-        unsigned __int128 t2 = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            t1 += red1[w];
-            t2 += ((unsigned __int128)red2[w][1] << 64) | red2[w][0];
-        }
-        a.part[blockIdx.x].s1 = t1;
-        a.part[blockIdx.x].s2_lo = (uint64_t)t2;
-        a.part[blockIdx.x].s2_hi = (uint64_t)(t2 >> 64);
-        a.part[blockIdx.x].flags = red_flag;
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t ent = tab[32u * (((e >> (4 * k)) & 0xFu) | (((o >> (4 * k)) & 0xFu) << 4))];
+        const int32_t S = (int32_t)(ent & 31u) - 8;
+        const int32_t A = (int32_t)((ent >> 5) & 127u) - 36;
+        const int32_t B = (int32_t)(ent >> 12);
+        sd += 8 * d + A;
+        sd2 += (int64_t)(8 * d * d + 2 * d * A + B);
+        d += S;
     }
 }
 
-__global__ void __launch_bounds__(256) k_obs_final(const ObsPartial *part, int n,
-                                                   const ObsPartial *col_flag, uint32_t L,
-                                                   uint64_t t, ObsDev *out)
+constexpr int kObsRowsWarps = 8;
+constexpr int kObsChunkRows = 256;            // rows of one block's chunk, at most
+constexpr int kObsChunkCap = kObsGridCap / 2; // chunk records fit the partials scratch
+
+// Column 0 is integrated chunk by chunk: with s(y) the sy- slope of site (0, y), U_c the sum of
+// s over the chunk's rows y >= 1, P_c the sum of U over the chunks before c and hl(y) the
+// chunk-local inclusive sum, h(0, y) = P_c + hl(y), so each chunk reports sums that only the
+// chunk-level prefix P_c completes.
+struct ObsChunk {
+    int64_t U, SA, Sh, Sh2, ShA;   // slope total; sums of A_y, hl, hl^2, hl A_y over the chunk
+    uint64_t SB_lo, SB_hi;         // sum of B_y (128-bit)
+    uint32_t n, flags;             // rows; bit 1 a row does not close, bit 2: s(0) = +1
+};
+static_assert(sizeof(ObsChunk) == 2 * sizeof(ObsPartial), "chunk records fill two partial slots");
+
+// Block b owns the contiguous rows [b L / G, (b+1) L / G); one warp per row, lane l walks words
+// [l W / 32, (l+1) W / 32) of the row's even-x plane (sublattice y & 1) and odd-x plane
+// (sublattice (y & 1) ^ 1), i.e. x in [64 j, 64 j + 64) for each owned word j.
+template <bool VEC>
+__global__ void __launch_bounds__(32 * kObsRowsWarps) k_obs_rows(const uint32_t *A, uint32_t L,
+                                                                ObsChunk *chunks)
 {
-    __shared__ long long s1w[8];
-    __shared__ unsigned long long s2w[8][2];
-    __shared__ uint32_t fw[8];
-    int64_t s1 = 0;
-    unsigned __int128 s2 = 0;
+    __shared__ uint32_t tabr[256 * 32];
+    __shared__ int64_t sA[kObsChunkRows];
+    __shared__ unsigned long long red2[kObsRowsWarps][2];
+    __shared__ uint32_t sbits[kObsChunkRows / 32];
+    __shared__ uint32_t red_flag;
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) {
+        const uint32_t v = nibble_pair_entry(i);
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) tabr[32 * i + l] = v;
+    }
+    if (threadIdx.x < kObsChunkRows / 32) sbits[threadIdx.x] = 0;
+    if (threadIdx.x == 0) red_flag = 0;
+    __syncthreads();
+    const uint32_t W = L / 64;
+    const size_t plane = (size_t)L * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t *tab = tabr + lane;
+    const uint32_t r0 = (uint32_t)(((uint64_t)blockIdx.x * L) / gridDim.x);
+    const uint32_t r1 = (uint32_t)(((uint64_t)(blockIdx.x + 1) * L) / gridDim.x);
+    const uint32_t c0 = (uint32_t)(((uint64_t)lane * W) / 32), c1 = (uint32_t)(((uint64_t)(lane + 1) * W) / 32);
+    const int64_t n = 64 * (int64_t)(c1 - c0);
+    unsigned __int128 sB = 0;
     uint32_t flags = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        s1 += part[i].s1;
-        s2 += ((unsigned __int128)part[i].s2_hi << 64) | part[i].s2_lo;
-        flags |= part[i].flags;
+    for (uint32_t y = r0 + warp; y < r1; y += kObsRowsWarps) {
+        const uint32_t se = y & 1u, so = se ^ 1u;
+        const uint32_t *pe = A + (size_t)(se * 2) * plane + (size_t)y * W;
+        const uint32_t *po = A + (size_t)(so * 2) * plane + (size_t)y * W;
+        int32_t d = 0, sd = 0;
+        int64_t sd2 = 0;
+        if constexpr (VEC) {
+            // chunks of a lane are a multiple of 4 words: 16-byte loads, four word pairs at a time
+            for (uint32_t j = c0; j < c1; j += 4) {
+                const uint4 e = *reinterpret_cast<const uint4 *>(pe + j);
+                const uint4 o = *reinterpret_cast<const uint4 *>(po + j);
+                obs_word_pair(tab, e.x, o.x, d, sd, sd2);
+                obs_word_pair(tab, e.y, o.y, d, sd, sd2);
+                obs_word_pair(tab, e.z, o.z, d, sd, sd2);
+                obs_word_pair(tab, e.w, o.w, d, sd, sd2);
+            }
+        } else {
+            for (uint32_t j = c0; j < c1; ++j) obs_word_pair(tab, pe[j], po[j], d, sd, sd2);
+        }
+        // place the lanes' pieces: E = offset before this lane's first site, from x = 0 inclusive
+        const int64_t incl = warp_incl_scan((int64_t)d);
+        const int64_t E = incl - d;
+        const int64_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        uint32_t w0 = 0, c = 0;
+        if (lane == 0) {
+            w0 = pe[0];
+            c = A[(size_t)(se * 2 + 1) * plane + (size_t)y * W] & 1u;
+        }
+        w0 = __shfl_sync(0xFFFFFFFFu, w0, 0);
+        // g(x) = h(x) - h(0) = offset(x) - s(0): the slope of site 0 is not part of h(0, y)
+        const int64_t G = E - (2 * (int64_t)(w0 & 1u) - 1);
+        const int64_t Ay = warp_sum(n * G + sd);
+        const int64_t By = warp_sum(n * G * G + 2 * G * (int64_t)sd + sd2);
+        if (lane == 0) {
+            sA[y - r0] = Ay;
+            if (c) atomicOr(&sbits[(y - r0) >> 5], 1u << ((y - r0) & 31));
+            sB += (unsigned __int128)(uint64_t)By;
+            if (total != 0) flags |= 2u;            // the row does not close around x
+        }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        s1 += __shfl_down_sync(0xFFFFFFFFu, s1, off);
-        const uint64_t lo = (uint64_t)s2, hi = (uint64_t)(s2 >> 64);
-        s2 += ((unsigned __int128)__shfl_down_sync(0xFFFFFFFFu, hi, off) << 64) |
-              __shfl_down_sync(0xFFFFFFFFu, lo, off);
-        flags |= __shfl_down_sync(0xFFFFFFFFu, flags, off);
-    }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        s1w[w] = s1;
-        s2w[w][0] = (uint64_t)s2;
-        s2w[w][1] = (uint64_t)(s2 >> 64);
-        fw[w] = flags;
+    if (lane == 0) {
+        red2[warp][0] = (uint64_t)sB;
+        red2[warp][1] = (uint64_t)(sB >> 64);
+        if (flags) atomicOr(&red_flag, flags);
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    __int128 S1 = 0;
-    unsigned __int128 S2 = 0;
-    flags = col_flag->flags;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-        S1 += s1w[k];
-        S2 += ((unsigned __int128)s2w[k][1] << 64) | s2w[k][0];
-        flags |= fw[k];
+    if (warp != 0) return;
+    // warp 0: the chunk's column sums; lane l takes rows [l m / 32, (l+1) m / 32) of the chunk
+    const uint32_t m = r1 - r0;
+    const uint32_t a0 = (uint32_t)(((uint64_t)lane * m) / 32), a1 = (uint32_t)(((uint64_t)(lane + 1) * m) / 32);
+    auto slope = [&](uint32_t i) -> int64_t {       // s(y) for y = r0 + i, 0 for y = 0
+        if (r0 + i == 0) return 0;
+        return 2 * (int64_t)((sbits[i >> 5] >> (i & 31)) & 1u) - 1;
+    };
+    int64_t u = 0;
+    for (uint32_t i = a0; i < a1; ++i) u += slope(i);
+    const int64_t ui = warp_incl_scan(u);
+    int64_t hl = ui - u;
+    int64_t SA = 0, Sh = 0, Sh2 = 0, ShA = 0;
+    for (uint32_t i = a0; i < a1; ++i) {
+        hl += slope(i);
+        const int64_t Ay = sA[i];
+        SA += Ay;
+        Sh += hl;
+        Sh2 += hl * hl;
+        ShA += hl * Ay;
     }
+    SA = warp_sum(SA);
+    Sh = warp_sum(Sh);
+    Sh2 = warp_sum(Sh2);
+    ShA = warp_sum(ShA);
+    const int64_t Utot = __shfl_sync(0xFFFFFFFFu, ui, 31);
+    if (lane == 0) {
+        unsigned __int128 t2 = 0;
+        for (int w = 0; w < kObsRowsWarps; ++w) t2 += ((unsigned __int128)red2[w][1] << 64) | red2[w][0];
+        ObsChunk ch;
+        ch.U = Utot;
+        ch.SA = SA;
+        ch.Sh = Sh;
+        ch.Sh2 = Sh2;
+        ch.ShA = ShA;
+        ch.SB_lo = (uint64_t)t2;
+        ch.SB_hi = (uint64_t)(t2 >> 64);
+        ch.n = m;
+        ch.flags = red_flag | ((r0 == 0 && (sbits[0] & 1u)) ? 4u : 0u);
+        chunks[blockIdx.x] = ch;
+    }
+}
+
+// One block: thread c takes chunk c, P_c = sum of U over earlier chunks (block scan), then
+//   S1 = sum_c L (n_c P_c + Sh_c) + SA_c,
+//   S2 = sum_c L (n_c P_c^2 + 2 P_c Sh_c + Sh2_c) + 2 (P_c SA_c + ShA_c) + SB_c,
+// num = N S2 - S1^2, all in 128-bit integers.  Flags: bit 0 column 0 does not close around y
+// (h(0, L-1) + s(0) != 0), bit 1 some row does not close around x.
+constexpr int kObsFinalThreads = 1024;
+
+__device__ __forceinline__ void block_sum_i128(__int128 &v, __int128 *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t lo = __shfl_xor_sync(0xFFFFFFFFu, (uint64_t)v, o);
+        const uint64_t hi = __shfl_xor_sync(0xFFFFFFFFu, (uint64_t)((unsigned __int128)v >> 64), o);
+        v += (__int128)(((unsigned __int128)hi << 64) | lo);
+    }
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __int128 t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        sh[0] = t;
+    }
+    __syncthreads();
+    v = sh[0];
+}
+
+__global__ void __launch_bounds__(kObsFinalThreads) k_obs_final(const ObsChunk *chunks, int nchunks,
+                                                                uint32_t L, uint64_t t, ObsDev *out)
+{
+    __shared__ __int128 sh[32];
+    __shared__ int64_t wsum[32];
+    __shared__ uint32_t fl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    ObsChunk ch{};
+    if (tid < nchunks) ch = chunks[tid];
+    const int64_t incl = warp_incl_scan(ch.U);
+    if (tid == 0) fl = 0;
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        v = warp_incl_scan(v);
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    const int64_t P = incl - ch.U + (warp > 0 ? wsum[warp - 1] : 0);
+    const int64_t col_total = wsum[(blockDim.x >> 5) - 1];
+    const __int128 Li = (__int128)L, Pi = (__int128)P, ni = (__int128)ch.n;
+    __int128 s1 = Li * (ni * Pi + ch.Sh) + ch.SA;
+    __int128 s2 = Li * (ni * Pi * Pi + 2 * Pi * ch.Sh + ch.Sh2) + 2 * (Pi * ch.SA + ch.ShA) +
+                  (__int128)(((unsigned __int128)ch.SB_hi << 64) | ch.SB_lo);
+    uint32_t flags = __reduce_or_sync(0xFFFFFFFFu, ch.flags);
+    if (lane == 0 && flags) atomicOr(&fl, flags);
+    block_sum_i128(s1, sh);
+    block_sum_i128(s2, sh);
+    if (tid != 0) return;
+    flags = fl;
+    // closure around the y cycle: h(0, L-1) + s(0) must return to h(0, 0) = 0
+    const int64_t s0 = (flags & 4u) ? 1 : -1;
+    flags &= 3u;
+    if (col_total + s0 != 0) flags |= 1u;
+    const unsigned __int128 S2 = (unsigned __int128)s2;
     const unsigned __int128 N = (unsigned __int128)L * L;
-    const unsigned __int128 num = N * S2 - (unsigned __int128)(S1 * S1);
+    const unsigned __int128 num = N * S2 - (unsigned __int128)(s1 * s1);
     out->t = t;
     out->N = (uint64_t)N;
-    out->S1 = (int64_t)S1;
+    out->S1 = (int64_t)s1;
     out->S2_lo = (uint64_t)S2;
     out->S2_hi = (uint64_t)(S2 >> 64);
     out->num_lo = (uint64_t)num;
@@ -267,26 +284,27 @@ __global__ void __launch_bounds__(256) k_obs_final(const ObsPartial *part, int n
 
 int obs_partials(uint32_t L)
 {
-    const TeamShape ts = team_shape(L / 64, 256);
-    const int grid = (int)((L + ts.teams - 1) / ts.teams);
-    const int cap = sm_count() * 8 < kObsGridCap ? sm_count() * 8 : kObsGridCap;
-    return grid < cap ? grid : cap;
+    // chunks of at most kObsChunkRows rows, at most kObsChunkCap of them, about 4 per SM
+    int g = sm_count() * 4;
+    if (g > kObsChunkCap) g = kObsChunkCap;
+    if ((uint32_t)g > L) g = (int)L;
+    while ((L + g - 1) / g > (uint32_t)kObsChunkRows) g *= 2;
+    return g;
 }
 
+// h0: unused (kept in the scratch layout); partials: the chunk records (two partial slots each).
 cudaError_t launch_observe(const uint32_t *A, uint32_t L, int64_t *h0, ObsPartial *partials,
                            ObsDev *result, uint64_t t, cudaStream_t st)
 {
+    (void)h0;
     const uint32_t W = L / 64;
-    const TeamShape ts = team_shape(W, 256);
     const int grid = obs_partials(L);
-    ObsPartial *col_flag = partials + grid;
-    k_obs_col0<<<1, 1024, 0, st>>>(A, L, h0, col_flag);
-    RowsArgs ra{A, L, W, ts.T, ts.TP, h0, partials};
-    if (ts.V == 4) k_obs_rows<4><<<grid, ts.block, 0, st>>>(ra);
-    else if (ts.V == 2) k_obs_rows<2><<<grid, ts.block, 0, st>>>(ra);
-    else k_obs_rows<1><<<grid, ts.block, 0, st>>>(ra);
-    k_obs_final<<<1, 256, 0, st>>>(partials, grid, col_flag, L, t, result);
-    count_launches(3);
+    if (grid > kObsChunkCap) return cudaErrorInvalidValue;
+    ObsChunk *chunks = reinterpret_cast<ObsChunk *>(partials);
+    if (W % 128 == 0) k_obs_rows<true><<<grid, 32 * kObsRowsWarps, 0, st>>>(A, L, chunks);
+    else k_obs_rows<false><<<grid, 32 * kObsRowsWarps, 0, st>>>(A, L, chunks);
+    k_obs_final<<<1, kObsFinalThreads, 0, st>>>(chunks, grid, L, t, result);
+    count_launches(2);
     return cudaGetLastError();
 }
 
