@@ -252,15 +252,28 @@ int sca_set_temporal_block(sca_sim *s, int mcs_per_launch)
 
 // Automatic kernel choice (measured on GB300).  For a surface state the register-wavefront
 // kernel (4) wins wherever the lattice gives it enough tiles: with {0, 1} probabilities from
-// L = 4096 on (8 MCS per launch up to L = 8192, 16 above), with dyadic draws from L = 65536 on
-// (2 MCS per launch; below that the fused kernel's HBM-bound pass is as fast).  Otherwise the
-// fused kernel halves HBM traffic once the state is far larger than L2 and the update is not
-// arithmetic-bound; shared-memory temporal blocking (several MCS per launch) wins while the
-// lattice is small enough that launches and L2 round trips dominate (dyadic draws up to
-// L = 8192, per-site uniforms up to L = 2048); the two-pass kernel covers the rest.
-static uint32_t wave_default_k(uint32_t L, int mode)
+// L = 4096 on (8 MCS per launch up to L = 8192, 16 above); with dyadic draws from L = 32768 on
+// for one or two draws per word (2 MCS per launch) and from L = 65536 on for three (1 MCS per
+// launch: the three Philox chains leave no registers for a deeper window); four or more draws
+// run at the fused kernel's speed or below.  Otherwise the fused kernel halves HBM traffic once
+// the state is far larger than L2 and the update is not arithmetic-bound; shared-memory
+// temporal blocking (several MCS per launch) wins while the lattice is small enough that
+// launches and L2 round trips dominate (dyadic draws up to L = 8192, per-site uniforms up to
+// L = 2048); the two-pass kernel covers the rest.
+static uint32_t wave_default_k(uint32_t L, const Rule &R)
 {
-    return mode == 0 ? (L >= 16384 ? 16u : 8u) : 2u;
+    if (R.mode == 0) return L >= 16384 ? 16u : 8u;
+    return R.n_draws >= 3 ? 1u : 2u;
+}
+
+static bool wave_auto(const sca_sim *s)
+{
+    if (!s->surface) return false;
+    const Rule &R = s->R;
+    if (R.mode == 0) return s->L >= 4096;
+    if (R.mode != 1 || s->L % 256 != 0) return false;
+    if (R.n_draws <= 2) return s->L >= 32768;
+    return R.n_draws == 3 && s->L >= 65536;
 }
 
 int sca::effective_kernel(const sca_sim *s, int *tb_k)
@@ -268,15 +281,14 @@ int sca::effective_kernel(const sca_sim *s, int *tb_k)
     int k = s->kernel;
     int kk = s->tb_k;
     const int mode = (int)s->R.mode;
-    if (k == 4) kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : wave_default_k(s->L, mode), mode);
+    if (k == 4) kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : wave_default_k(s->L, s->R), mode);
     if (k == 0) {
         uint32_t ns;
         size_t sm;
-        const bool wave_ok = s->surface && ((mode == 0 && s->L >= 4096) || (mode == 1 && s->L >= 65536)) &&
-                             wave_supported(s->L, wave_default_k(s->L, mode), mode);
+        const bool wave_ok = wave_auto(s) && wave_supported(s->L, wave_default_k(s->L, s->R), mode);
         if (wave_ok) {
             k = 4;
-            kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : wave_default_k(s->L, mode), mode);
+            kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : wave_default_k(s->L, s->R), mode);
         } else if (fused_supported(s->L) && s->L >= 32768 && s->R.mode != 2) {
             k = 2;
         } else if (s->R.mode != 2 && s->L <= 8192 && tblock_plan(s->L, s->tb_set ? kk : 8, &ns, &sm)) {

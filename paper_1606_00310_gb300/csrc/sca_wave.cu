@@ -7,7 +7,7 @@ namespace sca {
 
 // Dyadic instantiations (other translation unit, compiled in parallel); V words per lane.
 cudaError_t launch_wave_dyadic(const WaveArgs &a, int K, int V, int grid, cudaStream_t st);
-int wave_dyadic_blocks_per_sm(int K, int V);
+int wave_dyadic_blocks_per_sm(const Rule &R, int K, int V);
 
 // Words per lane: dyadic draws take four (one Philox call per draw for the four words) when
 // the row length allows, else one; {0, 1} probabilities one.
@@ -47,7 +47,7 @@ static cudaError_t launch_mode0(const WaveArgs &a, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-int wave_max_k(int mode) { return mode == 0 ? 16 : mode == 1 ? 4 : 0; }
+int wave_max_k(int mode) { return mode == 0 ? 16 : mode == 1 ? 2 : 0; }
 
 uint32_t wave_pick_k(uint32_t want, int mode)
 {
@@ -59,7 +59,7 @@ uint32_t wave_pick_k(uint32_t want, int mode)
 
 static int blocks_for(int K, int V, const Rule &R)
 {
-    if (R.mode == 1) return wave_dyadic_blocks_per_sm(K, V);
+    if (R.mode == 1) return wave_dyadic_blocks_per_sm(R, K, V);
     const bool dp = R.Pp != 0, dq = R.Pq != 0;
     switch (K) {
     case 1: return blocks_mode0<1>(dp, dq);

@@ -126,11 +126,57 @@ __device__ __forceinline__ void wave_xi(const Rule &R, uint64_t u0, uint64_t t, 
     }
 }
 
+// The same construction with the number of draws ND fixed at compile time, so the ND Philox
+// chains are independent straight-line code the scheduler interleaves; DP / DQ false when
+// p / q is exactly 0 (that word is then 0 and its test drops out of the update).
+template <int V, int ND, bool DP, bool DQ>
+__device__ __forceinline__ void wave_xi_fixed(const Rule &R, uint64_t u0, uint64_t t, int s,
+                                              uint32_t (&xp)[V], uint32_t (&xq)[V])
+{
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        xp[v] = (R.np == 0 && R.Pp) ? 0xFFFFFFFFu : 0u;
+        xq[v] = (R.nq == 0 && R.Pq) ? 0xFFFFFFFFu : 0u;
+    }
+#pragma unroll
+    for (int i = ND; i >= 1; --i) {
+        uint32_t r[V];
+        if constexpr (V == 4) {
+            const Ctr4 o = philox4x32_10_rk(draw_counter(u0 >> 2, t, s, i, 0), R.rk);
+            r[0] = o.x; r[1 % V] = o.y; r[2 % V] = o.z; r[3 % V] = o.w;
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const uint64_t u = u0 + v;
+                r[v] = lane_of(philox4x32_10_rk(draw_counter(u >> 2, t, s, i, 0), R.rk), (uint32_t)(u & 3));
+            }
+        }
+        if (DP && i <= (int)R.np) {
+            const bool first = (i == (int)R.np);
+            const bool bit = (R.Pp >> (R.np - i)) & 1u;
+#pragma unroll
+            for (int v = 0; v < V; ++v) xp[v] = first ? r[v] : (bit ? (r[v] | xp[v]) : (r[v] & xp[v]));
+        }
+        if (DQ && i <= (int)R.nq) {
+            const bool first = (i == (int)R.nq);
+            const bool bit = (R.Pq >> (R.nq - i)) & 1u;
+#pragma unroll
+            for (int v = 0; v < V; ++v) xq[v] = first ? r[v] : (bit ? (r[v] | xq[v]) : (r[v] & xq[v]));
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        if (!DP) xp[v] = 0u;
+        if (!DQ) xq[v] = 0u;
+    }
+}
+
 // V consecutive words per lane (V = 1, 2 or 4; the lattice's words per row must be a multiple
 // of V).  U rows per loop iteration: the loop body holds U x 2K half-step updates, and the row
 // window (2K+1+U slots) shifts by U slots per iteration.  MODE 0: p, q in {0, 1} with
-// DP = (p == 1), DQ = (q == 1); MODE 1: dyadic draws.
-template <int K, int V, int U, int MODE, bool DP, bool DQ>
+// DP = (p == 1), DQ = (q == 1); MODE 1: dyadic draws, ND of them fixed at compile time (0: the
+// rule's count at run time), DP / DQ = (p != 0) / (q != 0).
+template <int K, int V, int U, int MODE, bool DP, bool DQ, int ND = 0>
 __global__ void __launch_bounds__(32 * kWaveWarps) k_wave(const WaveArgs a)
 {
     constexpr int S = 2 * K;                    // half-steps per launch
@@ -261,7 +307,11 @@ __global__ void __launch_bounds__(32 * kWaveWarps) k_wave(const WaveArgs a)
                 uint32_t xp[V], xq[V];
                 if constexpr (MODE == 1) {
                     const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
-                    wave_xi<V>(a.R, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
+                    if constexpr (ND == 0)
+                        wave_xi<V>(a.R, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
+                    else
+                        wave_xi_fixed<V, ND, DP, DQ>(a.R, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1),
+                                                     s, xp, xq);
                 }
 #pragma unroll
                 for (int v = 0; v < V; ++v) {

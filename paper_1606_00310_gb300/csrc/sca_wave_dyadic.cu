@@ -1,45 +1,71 @@
 // Register-wavefront temporal blocking with dyadic draws (Sec. III): instantiations of the
 // height-bit kernel in sca_wave.cuh for MODE 1, kept in their own translation unit so they
-// compile in parallel with the rest of the library.
+// compile in parallel with the rest of the library.  Four words per lane (one Philox call per
+// draw covers them) with the draw count fixed at compile time for 1..3 draws and q = 0 or not;
+// everything else takes the run-time draw loop.
 #include "sca_wave.cuh"
 
 namespace sca {
 
-template <int K, int V>
-static int blocks_dyadic()
+template <int K, int V, bool DQ, int ND>
+static cudaError_t launch_one(const WaveArgs &a, int grid, cudaStream_t st, int *blocks)
 {
-    static int n = 0;
-    if (n == 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wave<K, V, kWaveU1, 1, true, true>, 32 * kWaveWarps, 0) !=
-                cudaSuccess || b <= 0)
-            b = 1;
-        n = b;
+    auto kern = k_wave<K, V, kWaveU1, 1, true, DQ, ND>;
+    if (blocks) {
+        static int n = 0;
+        if (n == 0) {
+            int b = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * kWaveWarps, 0) != cudaSuccess || b <= 0)
+                b = 1;
+            n = b;
+        }
+        *blocks = n;
+        return cudaSuccess;
     }
-    return n;
+    kern<<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
-int wave_dyadic_blocks_per_sm(int K, int V)
+template <int K>
+static cudaError_t dispatch_k(const WaveArgs &a, int V, int grid, cudaStream_t st, int *blocks)
 {
-    if (V == 4) return K == 1 ? blocks_dyadic<1, 4>() : K == 2 ? blocks_dyadic<2, 4>() : blocks_dyadic<4, 4>();
-    return K == 1 ? blocks_dyadic<1, 1>() : K == 2 ? blocks_dyadic<2, 1>() : blocks_dyadic<4, 1>();
+    const Rule &R = a.R;
+    const bool dp = !(R.np == 0 && R.Pp == 0), dq = !(R.nq == 0 && R.Pq == 0);
+    if (V == 4 && dp && R.n_draws >= 1 && R.n_draws <= 3) {
+        switch (R.n_draws * 2 + (dq ? 1 : 0)) {
+        case 2: return launch_one<K, 4, false, 1>(a, grid, st, blocks);
+        case 3: return launch_one<K, 4, true, 1>(a, grid, st, blocks);
+        case 4: return launch_one<K, 4, false, 2>(a, grid, st, blocks);
+        case 5: return launch_one<K, 4, true, 2>(a, grid, st, blocks);
+        case 6: return launch_one<K, 4, false, 3>(a, grid, st, blocks);
+        default: return launch_one<K, 4, true, 3>(a, grid, st, blocks);
+        }
+    }
+    if (V == 4) return launch_one<K, 4, true, 0>(a, grid, st, blocks);
+    return launch_one<K, 1, true, 0>(a, grid, st, blocks);
 }
 
-template <int V>
-static cudaError_t launch_v(const WaveArgs &a, int K, int grid, cudaStream_t st)
+static cudaError_t dispatch(const WaveArgs &a, int K, int V, int grid, cudaStream_t st, int *blocks)
 {
     switch (K) {
-    case 1: k_wave<1, V, kWaveU1, 1, true, true><<<grid, 32 * kWaveWarps, 0, st>>>(a); break;
-    case 2: k_wave<2, V, kWaveU1, 1, true, true><<<grid, 32 * kWaveWarps, 0, st>>>(a); break;
-    case 4: k_wave<4, V, kWaveU1, 1, true, true><<<grid, 32 * kWaveWarps, 0, st>>>(a); break;
+    case 1: return dispatch_k<1>(a, V, grid, st, blocks);
+    case 2: return dispatch_k<2>(a, V, grid, st, blocks);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+}
+
+int wave_dyadic_blocks_per_sm(const Rule &R, int K, int V)
+{
+    WaveArgs a{};
+    a.R = R;
+    int b = 1;
+    if (dispatch(a, K, V, 0, nullptr, &b) != cudaSuccess) return 1;
+    return b;
 }
 
 cudaError_t launch_wave_dyadic(const WaveArgs &a, int K, int V, int grid, cudaStream_t st)
 {
-    return V == 4 ? launch_v<4>(a, K, grid, st) : launch_v<1>(a, K, grid, st);
+    return dispatch(a, K, V, grid, st, nullptr);
 }
 
 }  // namespace sca

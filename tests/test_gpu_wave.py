@@ -44,6 +44,10 @@ WAVE_CASES = [
     (320, 0.5, 0.5, 8, 7), (2048, 0.75, 0.25, 8, 0), (1984, 0.625, 0.0, 2, 992),
     (4096, 1.0, 0.0, 8, 0), (4096, 0.5, 0.0, 1, 0), (8192, 0.9375, 0.0625, 8, 3),
     (6144, 1.0, 1.0, 4, 0), (3968, 0.75, 0.25, 2, 5),
+    # four words per lane with the draw count fixed at compile time (1..3 draws, q = 0 or not),
+    # p = 1 with dyadic q, and p = 0 (run-time draw loop)
+    (2048, 0.875, 0.125, 2, 0), (1024, 0.625, 0.0, 2, 3), (512, 0.5, 0.5, 1, 0),
+    (768, 0.75, 0.0, 2, 0), (1280, 1.0, 0.25, 2, 0), (1536, 0.0, 0.5, 2, 0),
 ]
 
 
