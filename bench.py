@@ -494,18 +494,53 @@ def run_ours(a, rank, world, local_rank):
             sim.get_state_ptr(host_out.data_ptr(), n_words)
             return obs
 
+        # one simulation, synchronous calls: copies and updates in sequence (context)
         e2e_step()
         sync_all()
         t0 = time.perf_counter()
         for _ in range(a.steps):
             e2e_step()
         sync_all()
+        seq_s = time.perf_counter() - t0
+        seq_value, seq_s = aggregate_replicas(updates_per_step * a.steps, seq_s, dist, dev)
+
+        # two simulations on two streams, asynchronous calls: step i's host copies overlap
+        # step i-1's updates on the other simulation; every copy is inside the timed region
+        stream2 = torch.cuda.Stream(device=dev)
+        sim2 = sca.Sim(L, seed=1 + rank, p=a.p, q=a.q, stream=stream2, kernel=a.kernel)
+        host_out2 = torch.empty(n_words, dtype=torch.int32, pin_memory=True)
+        sims, outs = [sim, sim2], [host_out, host_out2]
+
+        def pipelined(k):
+            pending = None
+            for i in range(k):
+                s = sims[i % 2]
+                s.set_state_ptr_async(host_in.data_ptr(), n_words, 0)
+                s.run_async(times)
+                s.get_state_ptr_async(outs[i % 2].data_ptr(), n_words)
+                if pending is not None:
+                    ob = pending.wait()
+                    assert ob[-1].t == a.mcs and all(o_.status == 0 for o_ in ob)
+                pending = s
+            ob = pending.wait()
+            assert ob[-1].t == a.mcs and all(o_.status == 0 for o_ in ob)
+
+        pipelined(2)
+        sync_all()
+        t0 = time.perf_counter()
+        pipelined(a.steps)
+        sync_all()
         e2e_s = time.perf_counter() - t0
+        sim2.close()
         e2e_value, e2e_s = aggregate_replicas(updates_per_step * a.steps, e2e_s, dist, dev)
         obs_bytes = len(times) * 72
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 4 * n_words, "d2h_bytes_per_step": 4 * n_words + obs_bytes,
-               "ms_per_step": 1000.0 * e2e_s / a.steps}
+               "ms_per_step": 1000.0 * e2e_s / a.steps,
+               "pipelined": "two simulations on two streams: sca_set_state_async (pinned 1 GiB "
+                            "in), sca_run_async, sca_get_state_async (1 GiB out), sca_wait",
+               "sequential_value": seq_value,
+               "sequential_ms_per_step": 1000.0 * seq_s / a.steps}
 
     # context: the paper's own benchmark case p = 1/2, q = 0 (random bits every update)
     extra = None

@@ -136,6 +136,27 @@ int sca_get_state(sca_sim *sim, uint32_t *host_words, size_t n_words);
  * sca_observe reports a state that does not close. */
 int sca_set_state(sca_sim *sim, const uint32_t *host_words, size_t n_words, uint64_t t);
 
+/* Asynchronous host I/O and runs, for pipelining: with two simulations on two streams, one
+ * simulation's state copies overlap the other's updates.  Each call only enqueues work on the
+ * simulation's stream and returns; host buffers must stay untouched until sca_wait returns
+ * (pinned memory makes the copies asynchronous; pageable memory works but copies in place).
+ *
+ * sca_set_state_async: as sca_set_state (same words, same t), including the surface check,
+ * whose verdict the next call that chooses a kernel collects (it waits for the copy and the
+ * check to finish).  Errors: SCA_EINVAL, SCA_ECUDA.
+ * sca_get_state_async: as sca_get_state, without the synchronisation.  Errors: SCA_EINVAL,
+ * SCA_ECUDA.
+ * sca_run_async: as sca_run with at most 64 times, without the synchronisation; the n
+ * observation records stay on the device until sca_wait (or the next run or observation).
+ * Errors: SCA_EINVAL, SCA_ECUDA, SCA_ESTATE (kernel 4 chosen for a state that is not a surface).
+ * sca_wait: synchronises the simulation's stream and copies the first n (<= the last
+ * sca_run_async's count) observation records to out.  Errors: SCA_EINVAL, SCA_ECUDA,
+ * SCA_ETIMEOUT, SCA_ESTATE (as sca_run). */
+int sca_set_state_async(sca_sim *sim, const uint32_t *host_words, size_t n_words, uint64_t t);
+int sca_get_state_async(sca_sim *sim, uint32_t *host_words, size_t n_words);
+int sca_run_async(sca_sim *sim, const uint64_t *times, uint32_t n);
+int sca_wait(sca_sim *sim, sca_obs *out, uint32_t n);
+
 /* Device pointer to the current canonical words (valid until the next call on sim).  Read
  * only: write a new state with sca_set_state. */
 int sca_state_device(sca_sim *sim, uint32_t **words_dev);

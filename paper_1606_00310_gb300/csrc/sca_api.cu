@@ -141,6 +141,10 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
     s->tb_set = false;
     s->wave_bands = 0;
     s->surface = true;
+    s->chk_host = nullptr;
+    s->chk_ev = nullptr;
+    s->chk_pending = false;
+    s->async_obs = 0;
     s->cur = 0;
     s->timing = false;
     s->timed_launches = 0;
@@ -198,6 +202,7 @@ int sca_reset(sca_sim *s)
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     s->t = 0;
     s->surface = true;
+    s->chk_pending = false;
     return SCA_OK;
 }
 
@@ -276,6 +281,18 @@ static bool wave_auto(const sca_sim *s)
     return R.n_draws == 3 && s->L >= 65536;
 }
 
+// An asynchronous state load decides `surface` when its check completes; the first decision
+// that needs it waits for that check (the copy and one pass over the state, on this stream).
+static int resolve_surface(sca_sim *s)
+{
+    if (!s->chk_pending) return SCA_OK;
+    cudaError_t e = cudaEventSynchronize(s->chk_ev);
+    if (e != cudaSuccess) return cuda_fail(e, "surface check");
+    s->surface = surface_from(s->chk_host, s->L);
+    s->chk_pending = false;
+    return SCA_OK;
+}
+
 int sca::effective_kernel(const sca_sim *s, int *tb_k)
 {
     int k = s->kernel;
@@ -338,12 +355,18 @@ int sca_set_fused_shape(sca_sim *s, int words_per_thread, int ring)
 int sca_get_kernel(const sca_sim *s)
 {
     if (!s) return fail(SCA_EINVAL, "NULL simulation");
+    int rc = resolve_surface(const_cast<sca_sim *>(s));
+    if (rc) return rc;
     return effective_kernel(s, nullptr);
 }
 
 int sca::step_impl(sca_sim *s, uint64_t n)
 {
     if (n == 0) return SCA_OK;
+    {
+        int rc = resolve_surface(s);
+        if (rc) return rc;
+    }
     int tbk = 0;
     const int kern = effective_kernel(s, &tbk);
     const bool fused = kern == 2;
@@ -492,7 +515,82 @@ int sca_set_state(sca_sim *s, const uint32_t *host_words, size_t n_words, uint64
     e = surface_check(s->buf[s->cur], s->L, reinterpret_cast<uint32_t *>(s->part), s->stream, &surf);
     if (e != cudaSuccess) return cuda_fail(e, "surface check");
     s->surface = surf;
+    s->chk_pending = false;
     s->t = t;
+    return SCA_OK;
+}
+
+int sca_set_state_async(sca_sim *s, const uint32_t *host_words, size_t n_words, uint64_t t)
+{
+    if (!s || !host_words) return fail(SCA_EINVAL, "NULL argument");
+    if (n_words * sizeof(uint32_t) != s->lo.state_bytes) return fail(SCA_EINVAL, "wrong word count");
+    if (!s->chk_host) {
+        cudaError_t e = cudaMallocHost(&s->chk_host, 4 * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->chk_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "sca_set_state_async");
+    }
+    cudaError_t e = cudaMemcpyAsync(s->buf[s->cur], host_words, s->lo.state_bytes,
+                                    cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = surface_check_async(s->buf[s->cur], s->L, reinterpret_cast<uint32_t *>(s->part), s->chk_host,
+                                s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->chk_ev, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sca_set_state_async");
+    s->chk_pending = true;
+    s->t = t;
+    return SCA_OK;
+}
+
+int sca_get_state_async(sca_sim *s, uint32_t *host_words, size_t n_words)
+{
+    if (!s || !host_words) return fail(SCA_EINVAL, "NULL argument");
+    if (n_words * sizeof(uint32_t) < s->lo.state_bytes) return fail(SCA_EINVAL, "host buffer too small");
+    cudaError_t e = cudaMemcpyAsync(host_words, s->buf[s->cur], s->lo.state_bytes,
+                                    cudaMemcpyDeviceToHost, s->stream);
+    return e == cudaSuccess ? SCA_OK : cuda_fail(e, "sca_get_state_async");
+}
+
+int sca_run_async(sca_sim *s, const uint64_t *times, uint32_t n)
+{
+    if (!s || (n && !times)) return fail(SCA_EINVAL, "NULL argument");
+    if (n > (uint32_t)kResCap) return fail(SCA_EINVAL, "at most 64 observation times per asynchronous run");
+    uint64_t prev = s->t;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (times[i] < prev) return fail(SCA_EINVAL, "observation times must be non-decreasing");
+        prev = times[i];
+    }
+    s->async_obs = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        int rc = step_impl(s, times[i] - s->t);
+        if (rc) return rc;
+        cudaError_t e = launch_observe(s->buf[s->cur], s->L, s->h0, s->part, s->res + i, s->t, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "observe launch");
+    }
+    s->async_obs = n;
+    return SCA_OK;
+}
+
+int sca_wait(sca_sim *s, sca_obs *out, uint32_t n)
+{
+    if (!s || (n && !out)) return fail(SCA_EINVAL, "NULL argument");
+    if (n > s->async_obs) return fail(SCA_EINVAL, "more records than the last asynchronous run made");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sca_wait");
+    uint32_t err = 0;
+    e = cudaMemcpy(&err, s->err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && n) e = cudaMemcpy(out, s->res, n * sizeof(ObsDev), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "sca_wait");
+    s->async_obs = 0;
+    if (err) {
+        cudaMemset(s->err, 0, sizeof(uint32_t));
+        return fail(SCA_ETIMEOUT, "an update kernel's pipeline wait gave up; state invalid");
+    }
+    int first_bad = SCA_OK;
+    for (uint32_t i = 0; i < n; ++i) {
+        finish_obs(out[i]);
+        if (out[i].status && !first_bad) first_bad = out[i].status;
+    }
+    if (first_bad) return fail(first_bad, "slopes do not close around the torus");
     return SCA_OK;
 }
 
@@ -543,6 +641,8 @@ void sca_free(sca_sim *s)
         cudaStreamSynchronize(s->stream);
     }
     if (s->own_mem) cudaFree(s->base);
+    if (s->chk_host) cudaFreeHost(s->chk_host);
+    if (s->chk_ev) cudaEventDestroy(s->chk_ev);
     delete s;
 }
 

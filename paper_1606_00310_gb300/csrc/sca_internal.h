@@ -68,6 +68,11 @@ uint32_t wave_pick_k(uint32_t want, int mode);   // largest supported power of t
 // words of device scratch; synchronises the stream.
 cudaError_t surface_check(const uint32_t *A, uint32_t L, uint32_t *scratch, cudaStream_t st,
                           bool *is_surface);
+// The same check enqueued only: the three result words land in host3 (pinned) when the stream
+// gets there; surface_from() reads them.
+cudaError_t surface_check_async(const uint32_t *A, uint32_t L, uint32_t *scratch, uint32_t *host3,
+                                cudaStream_t st);
+bool surface_from(const uint32_t *host3, uint32_t L);
 bool fused_shape_ok(uint32_t L, int V, int ring);
 size_t fused_smem_bytes(uint32_t L);
 
@@ -113,6 +118,10 @@ struct sca_sim {
     bool tb_set;                      // tb_k chosen by the caller (else automatic)
     uint32_t wave_bands;              // row bands of the register-wavefront kernel (0 = auto)
     bool surface;                     // the state is known to be a surface (kernel 4 needs it)
+    uint32_t *chk_host;               // pinned: result of an enqueued surface check (or null)
+    cudaEvent_t chk_ev;               // recorded after that check's result copy
+    bool chk_pending;                 // surface is decided by that check once it completes
+    uint32_t async_obs;               // records of the last sca_run_async not yet collected
     bool timing;
     std::vector<cudaEvent_t> ev;      // start/stop pairs around update launches
     uint64_t timed_launches;

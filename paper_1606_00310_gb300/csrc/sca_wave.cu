@@ -152,6 +152,24 @@ __global__ void k_surface_check(const uint32_t *A, uint32_t L, uint32_t W, uint3
     }
 }
 
+bool surface_from(const uint32_t *h, uint32_t L) { return h[0] == 0 && h[1] == L / 2 && h[2] == L / 2; }
+
+cudaError_t surface_check_async(const uint32_t *A, uint32_t L, uint32_t *scratch, uint32_t *host3,
+                                cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const uint32_t W = L / 64;
+    const size_t n = 2 * (size_t)L * W;
+    int grid = (int)((n + 255) / 256);
+    if (grid > sm_count() * 8) grid = sm_count() * 8;
+    k_surface_check<<<grid, 256, 0, st>>>(A, L, W, scratch);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(host3, scratch, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+}
+
 cudaError_t surface_check(const uint32_t *A, uint32_t L, uint32_t *scratch, cudaStream_t st,
                           bool *is_surface)
 {
@@ -169,7 +187,7 @@ cudaError_t surface_check(const uint32_t *A, uint32_t L, uint32_t *scratch, cuda
     e = cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
-    *is_surface = h[0] == 0 && h[1] == L / 2 && h[2] == L / 2;
+    *is_surface = surface_from(h, L);
     return cudaSuccess;
 }
 

@@ -62,6 +62,10 @@ SIGNATURES = {
     "sca_set_fused_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "sca_set_temporal_block": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_set_wave_bands": (C.c_int, [C.c_void_p, C.c_int]),
+    "sca_set_state_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint64]),
+    "sca_get_state_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "sca_run_async": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.c_uint32]),
+    "sca_wait": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32]),
     "sca_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     "sca_free": (None, [C.c_void_p]),
@@ -279,6 +283,32 @@ class Sim:
 
     def get_state_ptr(self, host_ptr: int, n_words: int):
         check(load().sca_get_state(self._h, C.c_void_p(host_ptr), int(n_words)), "sca_get_state")
+
+    # -- asynchronous host I/O and runs (enqueue only; collect with wait())
+    def set_state_ptr_async(self, host_ptr: int, n_words: int, t: int = 0):
+        check(load().sca_set_state_async(self._h, C.c_void_p(host_ptr), int(n_words), int(t)),
+              "sca_set_state_async")
+
+    def get_state_ptr_async(self, host_ptr: int, n_words: int):
+        check(load().sca_get_state_async(self._h, C.c_void_p(host_ptr), int(n_words)),
+              "sca_get_state_async")
+
+    def run_async(self, times):
+        times = [int(x) for x in times]
+        n = len(times)
+        arr = (C.c_uint64 * n)(*times)
+        check(load().sca_run_async(self._h, arr, n), "sca_run_async")
+        self._async_n = n
+
+    def wait(self):
+        """Synchronise and return the last run_async's observations."""
+        n = getattr(self, "_async_n", 0)
+        out = (sca_obs * max(n, 1))()
+        rc = load().sca_wait(self._h, C.cast(out, C.c_void_p), n)
+        self._async_n = 0
+        if rc not in (OK, ESTATE):
+            check(rc, "sca_wait")
+        return [Obs.from_c(out[i]) for i in range(n)]
 
     def state_tensor(self):
         """The current canonical words as a uint32-viewed slice of the workspace tensor."""
