@@ -233,6 +233,18 @@ int sca_batch_init(const sca_params *params, uint32_t count, void *stream, sca_b
  * identical results; sca_batch_tune picks the fastest.  Errors: SCA_EINVAL when a lattice does
  * not fit the cluster's shared memory. */
 int sca_batch_set_shape(sca_batch *b, int cluster, int threads);
+
+/* Engine of the batch: 1 = clusters (every lattice in shared memory for the whole run, as height
+ * bits, split by rows over the CTAs of a thread-block cluster; any lattice of the batch limits),
+ * 2 = streaming (lattices grouped by size and rule; each group of lanes of a warp holds whole
+ * rows of one lattice and streams a band of its rows through registers for up to 8 MCS per
+ * launch; needs L a power-of-two multiple of 64 up to 2048 and dyadic or {0, 1} probabilities
+ * for every lattice), 0 = automatic (streaming when every lattice fits it, else clusters;
+ * sca_batch_tune picks the faster).  Results do not depend on the engine.  Errors: SCA_EINVAL
+ * (unknown engine, or streaming requested for a batch it does not fit). */
+int sca_batch_set_engine(sca_batch *b, int engine);
+/* Engine the next run uses (1 or 2). */
+int sca_batch_get_engine(const sca_batch *b);
 int sca_batch_get_shape(const sca_batch *b, int *cluster, int *threads, int *clusters_launched,
                         int *units);
 

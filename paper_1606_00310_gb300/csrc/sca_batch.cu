@@ -1060,6 +1060,23 @@ struct sca_batch {
     uint64_t t = 0;
     int C = 8, threads = 512, clusters = 0;
     size_t smem = 0, cap = 0;
+    // streaming engine: lattices grouped by (size, rule) into classes, each run as its own
+    // chain of launches on its own stream
+    int engine = 0;                    // requested: 0 automatic, 1 clusters, 2 streaming
+    uint32_t *state2 = nullptr;        // second state buffer (ping-pong)
+    struct WBClass {
+        uint32_t L = 0, n_lat = 0, rows = 0, n_items = 0;
+        Rule R{};
+        WBItem *items = nullptr;       // device
+        uint64_t *off = nullptr;       // device: members' state offsets
+        uint32_t *dst = nullptr;       // device: members' lattice indices
+        void *chunks = nullptr;        // device: observation scratch
+        cudaStream_t st = nullptr;
+        cudaEvent_t done = nullptr;
+    };
+    std::vector<WBClass> classes;
+    cudaEvent_t fork = nullptr;
+    bool wb_ready = false;
     // captured run (reused while the observation times and start time repeat)
     cudaGraphExec_t graph = nullptr;
     std::vector<uint64_t> graph_times;
@@ -1245,8 +1262,168 @@ int sca_batch_get_shape(const sca_batch *b, int *cluster, int *threads, int *clu
     return SCA_OK;
 }
 
+// ------------------------------------------------------------------ streaming engine (host)
+static bool same_rule(const Rule &a, const Rule &c)
+{
+    return a.mode == c.mode && a.n_draws == c.n_draws && a.np == c.np && a.nq == c.nq && a.Pp == c.Pp &&
+           a.Pq == c.Pq && a.Tp == c.Tp && a.Tq == c.Tq;
+}
+
+static bool wb_supported(const sca_batch *b)
+{
+    for (uint32_t i = 0; i < b->count; ++i)
+        if (!wave_batch_supported(b->lat[i].L, b->lat[i].R)) return false;
+    return true;
+}
+
+static void wb_free(sca_batch *b)
+{
+    for (auto &c : b->classes) {
+        cudaFree(c.items);
+        cudaFree(c.off);
+        cudaFree(c.dst);
+        cudaFree(c.chunks);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    // streams are shared between classes: destroy each once
+    std::vector<cudaStream_t> seen;
+    for (auto &c : b->classes)
+        if (c.st && std::find(seen.begin(), seen.end(), c.st) == seen.end()) seen.push_back(c.st);
+    for (cudaStream_t s : seen) cudaStreamDestroy(s);
+    b->classes.clear();
+    if (b->fork) cudaEventDestroy(b->fork);
+    b->fork = nullptr;
+    cudaFree(b->state2);
+    b->state2 = nullptr;
+    b->wb_ready = false;
+}
+
+// Classes of equal (L, rule); bands of at most 512 rows (an even count, equal within a class);
+// one work item per (lattice, band).
+static int wb_setup(sca_batch *b)
+{
+    if (b->wb_ready) return SCA_OK;
+    std::vector<int> cls(b->count, -1);
+    std::vector<std::vector<uint32_t>> members;
+    std::vector<sca_batch::WBClass> classes;
+    for (uint32_t i = 0; i < b->count; ++i) {
+        int c = -1;
+        for (size_t k = 0; k < classes.size(); ++k)
+            if (classes[k].L == b->lat[i].L && same_rule(classes[k].R, b->lat[i].R)) { c = (int)k; break; }
+        if (c < 0) {
+            sca_batch::WBClass nc;
+            nc.L = b->lat[i].L;
+            nc.R = b->lat[i].R;
+            classes.push_back(nc);
+            members.emplace_back();
+            c = (int)classes.size() - 1;
+        }
+        members[c].push_back(i);
+    }
+    b->classes = classes;
+    cudaError_t e = cudaMalloc(&b->state2, b->state_words * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    const int n_streams = (int)std::min<size_t>(16, classes.size());
+    std::vector<cudaStream_t> streams(n_streams, nullptr);
+    for (int s = 0; s < n_streams && e == cudaSuccess; ++s)
+        e = cudaStreamCreateWithFlags(&streams[s], cudaStreamNonBlocking);
+    for (size_t k = 0; k < b->classes.size() && e == cudaSuccess; ++k) {
+        auto &c = b->classes[k];
+        c.st = streams[k % n_streams];
+        c.n_lat = (uint32_t)members[k].size();
+        // bands: enough work items for about one wave of warps per launch (a class's launches
+        // form a chain, so a launch must not be a long sweep of few warps), but bands of at
+        // least 4K + 8 rows (rounded to a power of two) so the recomputed halo stays moderate
+        const uint32_t kmax = (uint32_t)wave_batch_max_k(c.R);
+        uint32_t min_rows = 1;
+        while (min_rows < 4 * kmax + 8) min_rows *= 2;
+        const uint32_t V = (c.R.mode == 1 && (c.L / 64) % 4 == 0) ? 4u : 1u;
+        const uint32_t groups_per_warp = 32u / ((c.L / 64) / V);
+        const uint64_t want_items = (uint64_t)groups_per_warp * (uint64_t)sm_count() * 16u;
+        uint32_t bands = 1;
+        while ((uint64_t)c.n_lat * bands < want_items && c.L / (2 * bands) >= min_rows &&
+               (c.L / (2 * bands)) % 2 == 0)
+            bands *= 2;
+        c.rows = c.L / bands;
+        std::vector<WBItem> items;
+        std::vector<uint64_t> off;
+        std::vector<uint32_t> dst;
+        for (uint32_t m : members[k]) {
+            const uint64_t seed = b->P[m].seed;
+            for (uint32_t q = 0; q < bands; ++q)
+                items.push_back(WBItem{b->state_off[m], (uint32_t)seed, (uint32_t)(seed >> 32), q * c.rows, 0u});
+            off.push_back(b->state_off[m]);
+            dst.push_back(m);
+        }
+        c.n_items = (uint32_t)items.size();
+        e = cudaMalloc(&c.items, items.size() * sizeof(WBItem));
+        if (e == cudaSuccess) e = cudaMalloc(&c.off, off.size() * sizeof(uint64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&c.dst, dst.size() * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&c.chunks, obs_batch_scratch_bytes(c.n_lat, c.L));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c.items, items.data(), items.size() * sizeof(WBItem), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c.off, off.data(), off.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c.dst, dst.data(), dst.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        // streams created so far belong to the classes (or to nobody if setup failed early)
+        for (auto &c : b->classes) c.st = nullptr;
+        for (cudaStream_t s : streams) if (s) cudaStreamDestroy(s);
+        wb_free(b);
+        return cuda_fail(e, "streaming batch setup");
+    }
+    b->wb_ready = true;
+    return SCA_OK;
+}
+
+static bool use_streaming(const sca_batch *b)
+{
+    if (b->engine == 1) return false;
+    return wb_supported(b);        // requested (2) or automatic (0): whenever every class fits
+}
+
+// Every class is an independent chain on its own stream: launches of up to K MCS between the
+// observation times, the class's observation at each time, and a copy back into the first
+// state buffer if the chain ended in the second.
+static int wb_enqueue(sca_batch *b, uint32_t n)
+{
+    cudaError_t e = cudaEventRecord(b->fork, b->stream);
+    for (auto &c : b->classes) {
+        if (e != cudaSuccess) break;
+        e = cudaStreamWaitEvent(c.st, b->fork, 0);
+        uint64_t t = b->t;
+        int cur = 0;
+        uint32_t *buf[2] = {b->state, b->state2};
+        const uint32_t kmax = (uint32_t)wave_batch_max_k(c.R);
+        for (uint32_t ob = 0; ob < n && e == cudaSuccess; ++ob) {
+            const uint64_t T = b->graph_times[ob];
+            while (t < T && e == cudaSuccess) {
+                uint32_t k = 1;
+                while (2 * k <= kmax && 2 * k <= T - t) k *= 2;
+                e = launch_wave_batch(buf[cur], buf[cur ^ 1], c.items, c.n_items, c.L, c.rows, t, k, c.R, c.st);
+                cur ^= 1;
+                t += k;
+            }
+            if (e == cudaSuccess)
+                e = launch_observe_batch(buf[cur], c.off, c.n_lat, c.L, c.chunks, c.dst, n, b->res + ob, T, c.st);
+        }
+        if (e == cudaSuccess && cur == 1) e = launch_wave_batch_copy(b->state2, b->state, c.items, c.n_items, c.L, c.st);
+        if (e == cudaSuccess) e = cudaEventRecord(c.done, c.st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, c.done, 0);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->res_h, b->res, (size_t)b->count * n * sizeof(ObsDev), cudaMemcpyDeviceToHost, b->stream);
+    return e == cudaSuccess ? SCA_OK : cuda_fail(e, "streaming batch launch");
+}
+
 static int batch_enqueue(sca_batch *b, uint32_t n)
 {
+    if (use_streaming(b)) {
+        int rc = wb_setup(b);
+        if (rc) return rc;
+        return wb_enqueue(b, n);
+    }
     BatchArgs a;
     a.state = b->state;
     a.lat = b->lat_d;
@@ -1269,6 +1446,23 @@ static int batch_enqueue(sca_batch *b, uint32_t n)
     return e == cudaSuccess ? SCA_OK : cuda_fail(e, "batch launch");
 }
 
+int sca_batch_set_engine(sca_batch *b, int engine)
+{
+    if (!b || engine < 0 || engine > 2) return fail(SCA_EINVAL, "engine must be 0, 1 or 2");
+    if (engine == 2 && !wb_supported(b))
+        return fail(SCA_EINVAL, "the streaming engine needs L <= 2048 with a power-of-two row length "
+                                "and dyadic or {0, 1} probabilities for every lattice");
+    b->engine = engine;
+    batch_drop_graph(b);
+    return SCA_OK;
+}
+
+int sca_batch_get_engine(const sca_batch *b)
+{
+    if (!b) return fail(SCA_EINVAL, "NULL batch");
+    return use_streaming(b) ? 2 : 1;
+}
+
 int sca_batch_run(sca_batch *b, const uint64_t *times, uint32_t n, sca_obs *out, double *ensemble_w2)
 {
     if (!b || !times || n == 0) return fail(SCA_EINVAL, "NULL argument or no times");
@@ -1286,11 +1480,16 @@ int sca_batch_run(sca_batch *b, const uint64_t *times, uint32_t n, sca_obs *out,
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "batch times");
         cudaGraph_t g = nullptr;
+        b->graph_times = tv;
+        if (use_streaming(b)) {
+            rc = wb_setup(b);                // allocations happen outside the capture
+            if (rc) return rc;
+        }
         e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
         rc = batch_enqueue(b, n);
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (rc) { if (g) cudaGraphDestroy(g); b->graph_times.clear(); return rc; }
         if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
         e = cudaGraphInstantiate(&b->graph, g, 0);
         cudaGraphDestroy(g);
@@ -1366,6 +1565,9 @@ int sca_batch_tune(sca_batch *b, uint32_t probe_mcs, int *best_cluster, int *bes
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(SCA_ECUDA, "cudaEventCreate");
+    const int requested = b->engine;
+    b->engine = 1;                               // the shapes are the cluster engine's
+    batch_drop_graph(b);
     for (const Shape &sh : shapes) {
         if (batch_plan(b, sh.c, sh.t, sh.cap) != SCA_OK) continue;   // shape does not fit: skip
         int rc = sca_batch_reset(b);
@@ -1380,8 +1582,27 @@ int sca_batch_tune(sca_batch *b, uint32_t probe_mcs, int *best_cluster, int *bes
             continue;
         if (ms < best) { best = ms; bs = sh; }
     }
+    // the streaming engine, when every lattice fits it; automatic choice takes the faster
+    int engine = 1;
+    if (wb_supported(b)) {
+        b->engine = 2;
+        batch_drop_graph(b);
+        int rc = sca_batch_reset(b);
+        const uint64_t tt = probe_mcs;
+        cudaEventRecord(e0, b->stream);
+        if (!rc) rc = sca_batch_run(b, &tt, 1, nullptr, nullptr);
+        cudaEventRecord(e1, b->stream);
+        float ms = 0.f;
+        if (!rc && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms < best) {
+            best = ms;
+            engine = 2;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    b->engine = requested == 0 ? engine : requested;
+    batch_drop_graph(b);
     int rc = batch_plan(b, bs.c, bs.t, bs.cap);
     if (!rc) rc = sca_batch_reset(b);
     if (rc) return rc;
@@ -1404,6 +1625,7 @@ void sca_batch_free(sca_batch *b)
     cudaFree(b->part);
     cudaFree(b->res);
     if (b->res_h) cudaFreeHost(b->res_h);
+    wb_free(b);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -76,6 +76,27 @@ bool surface_from(const uint32_t *host3, uint32_t L);
 bool fused_shape_ok(uint32_t L, int V, int ring);
 size_t fused_smem_bytes(uint32_t L);
 
+// Streaming engine of the batch (sca_wave_batch.cu): one work item per (lattice, band).
+struct WBItem {
+    uint64_t off;       // first canonical word of the lattice in the batch state buffers
+    uint32_t k0, k1;    // the lattice's Philox key (seed low / high)
+    uint32_t y0;        // first row of the band
+    uint32_t pad;
+};
+bool wave_batch_supported(uint32_t L, const Rule &R);
+int wave_batch_max_k(const Rule &R);
+cudaError_t launch_wave_batch(const uint32_t *src, uint32_t *dst, const WBItem *items, uint32_t n_items,
+                              uint32_t L, uint32_t rows_per_band, uint64_t t0, uint32_t k, const Rule &R,
+                              cudaStream_t st);
+cudaError_t launch_wave_batch_copy(const uint32_t *src, uint32_t *dst, const WBItem *items, uint32_t n_items,
+                                   uint32_t L, cudaStream_t st);
+// Batched observation of n_lat lattices of size L (first words at base + off[i]); record of
+// lattice i to out[dst[i] * stride]; chunk scratch of obs_batch_scratch_bytes(n_lat, L).
+cudaError_t launch_observe_batch(const uint32_t *base, const uint64_t *off, uint32_t n_lat, uint32_t L,
+                                 void *chunk_scratch, const uint32_t *dst, uint32_t stride, ObsDev *out,
+                                 uint64_t t, cudaStream_t st);
+size_t obs_batch_scratch_bytes(uint32_t n_lat, uint32_t L);
+
 // Observation kernels: h0 scratch of L int64; partials scratch of obs_partials(L) + 1 entries
 // (never more than kObsGridCap + 1).
 constexpr int kObsGridCap = 2048;

@@ -85,12 +85,11 @@ struct ObsChunk {
 };
 static_assert(sizeof(ObsChunk) == 2 * sizeof(ObsPartial), "chunk records fill two partial slots");
 
-// Block b owns the contiguous rows [b L / G, (b+1) L / G); one warp per row, lane l walks words
-// [l W / 32, (l+1) W / 32) of the row's even-x plane (sublattice y & 1) and odd-x plane
-// (sublattice (y & 1) ^ 1), i.e. x in [64 j, 64 j + 64) for each owned word j.
+// One block reduces the contiguous rows [r0, r1) of the lattice A: one warp per row, lane l
+// walks words [l W / 32, (l+1) W / 32) of the row's even-x plane (sublattice y & 1) and odd-x
+// plane (sublattice (y & 1) ^ 1), i.e. x in [64 j, 64 j + 64) for each owned word j.
 template <bool VEC>
-__global__ void __launch_bounds__(32 * kObsRowsWarps) k_obs_rows(const uint32_t *A, uint32_t L,
-                                                                ObsChunk *chunks)
+__device__ void obs_rows_chunk(const uint32_t *A, uint32_t L, uint32_t r0, uint32_t r1, ObsChunk *chunk)
 {
     __shared__ uint32_t tabr[256 * 32];
     __shared__ int64_t sA[kObsChunkRows];
@@ -109,8 +108,6 @@ __global__ void __launch_bounds__(32 * kObsRowsWarps) k_obs_rows(const uint32_t 
     const size_t plane = (size_t)L * W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t *tab = tabr + lane;
-    const uint32_t r0 = (uint32_t)(((uint64_t)blockIdx.x * L) / gridDim.x);
-    const uint32_t r1 = (uint32_t)(((uint64_t)(blockIdx.x + 1) * L) / gridDim.x);
     const uint32_t c0 = (uint32_t)(((uint64_t)lane * W) / 32), c1 = (uint32_t)(((uint64_t)(lane + 1) * W) / 32);
     const int64_t n = 64 * (int64_t)(c1 - c0);
     unsigned __int128 sB = 0;
@@ -200,8 +197,28 @@ __global__ void __launch_bounds__(32 * kObsRowsWarps) k_obs_rows(const uint32_t 
         ch.SB_hi = (uint64_t)(t2 >> 64);
         ch.n = m;
         ch.flags = red_flag | ((r0 == 0 && (sbits[0] & 1u)) ? 4u : 0u);
-        chunks[blockIdx.x] = ch;
+        *chunk = ch;
     }
+}
+
+// Block b owns the contiguous rows [b L / G, (b+1) L / G) of the lattice.
+template <bool VEC>
+__global__ void __launch_bounds__(32 * kObsRowsWarps) k_obs_rows(const uint32_t *A, uint32_t L,
+                                                                ObsChunk *chunks)
+{
+    const uint32_t r0 = (uint32_t)(((uint64_t)blockIdx.x * L) / gridDim.x);
+    const uint32_t r1 = (uint32_t)(((uint64_t)(blockIdx.x + 1) * L) / gridDim.x);
+    obs_rows_chunk<VEC>(A, L, r0, r1, chunks + blockIdx.x);
+}
+
+// Many lattices of one size: block b takes chunk b % nch of lattice b / nch (first word at
+// base + off[lattice]).
+__global__ void __launch_bounds__(32 * kObsRowsWarps) k_obs_rows_batch(const uint32_t *base, const uint64_t *off,
+                                                                      uint32_t L, uint32_t nch, ObsChunk *chunks)
+{
+    const uint32_t li = blockIdx.x / nch, c = blockIdx.x - li * nch;
+    const uint32_t r0 = (uint32_t)(((uint64_t)c * L) / nch), r1 = (uint32_t)(((uint64_t)(c + 1) * L) / nch);
+    obs_rows_chunk<false>(base + off[li], L, r0, r1, chunks + blockIdx.x);
 }
 
 // One block: thread c takes chunk c, P_c = sum of U over earlier chunks (block scan), then
@@ -280,6 +297,83 @@ __global__ void __launch_bounds__(kObsFinalThreads) k_obs_final(const ObsChunk *
     out->w2 = 0.0;
     out->status = flags ? -7 : 0;   // SCA_ESTATE
     out->reserved = (int32_t)flags;
+}
+
+// Many lattices: one warp per lattice combines its nch (<= 32) chunk records as k_obs_final
+// does and writes the record to out[dst[lattice] * stride].
+__device__ __forceinline__ __int128 warp_sum_i128(__int128 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t lo = __shfl_xor_sync(0xFFFFFFFFu, (uint64_t)v, o);
+        const uint64_t hi = __shfl_xor_sync(0xFFFFFFFFu, (uint64_t)((unsigned __int128)v >> 64), o);
+        v += (__int128)(((unsigned __int128)hi << 64) | lo);
+    }
+    return v;
+}
+
+__global__ void k_obs_final_batch(const ObsChunk *chunks, uint32_t nch, uint32_t n_lat, uint32_t L, uint64_t t,
+                                  const uint32_t *dst, uint32_t stride, ObsDev *out)
+{
+    const uint32_t li = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x & 31;
+    if (li >= n_lat) return;                                   // whole warp
+    ObsChunk ch{};
+    if ((uint32_t)lane < nch) ch = chunks[(size_t)li * nch + lane];
+    const int64_t incl = warp_incl_scan(ch.U);
+    const int64_t P = incl - ch.U;
+    const int64_t col_total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const __int128 Li = (__int128)L, Pi = (__int128)P, ni = (__int128)ch.n;
+    const __int128 s1 = warp_sum_i128(Li * (ni * Pi + ch.Sh) + ch.SA);
+    const __int128 s2 = warp_sum_i128(Li * (ni * Pi * Pi + 2 * Pi * ch.Sh + ch.Sh2) + 2 * (Pi * ch.SA + ch.ShA) +
+                                      (__int128)(((unsigned __int128)ch.SB_hi << 64) | ch.SB_lo));
+    uint32_t flags = __reduce_or_sync(0xFFFFFFFFu, ch.flags);
+    if (lane != 0) return;
+    const int64_t s0 = (flags & 4u) ? 1 : -1;
+    flags &= 3u;
+    if (col_total + s0 != 0) flags |= 1u;
+    const unsigned __int128 S2 = (unsigned __int128)s2;
+    const unsigned __int128 N = (unsigned __int128)L * L;
+    const unsigned __int128 num = N * S2 - (unsigned __int128)(s1 * s1);
+    ObsDev o;
+    o.t = t;
+    o.N = (uint64_t)N;
+    o.S1 = (int64_t)s1;
+    o.S2_lo = (uint64_t)S2;
+    o.S2_hi = (uint64_t)(S2 >> 64);
+    o.num_lo = (uint64_t)num;
+    o.num_hi = (uint64_t)(num >> 64);
+    o.w2 = 0.0;
+    o.status = flags ? -7 : 0;   // SCA_ESTATE
+    o.reserved = (int32_t)flags;
+    out[(size_t)dst[li] * stride] = o;
+}
+
+// Chunks per lattice for the batched observation (rows per chunk at most kObsChunkRows,
+// at most 32 chunks).
+uint32_t obs_batch_chunks(uint32_t L)
+{
+    uint32_t nch = 1;
+    while ((L + nch - 1) / nch > (uint32_t)kObsChunkRows && nch < 32) nch *= 2;
+    if (L >= 1024 && nch < 4) nch = 4;          // keep enough blocks for small ensembles
+    return nch;
+}
+
+cudaError_t launch_observe_batch(const uint32_t *base, const uint64_t *off, uint32_t n_lat, uint32_t L,
+                                 void *chunk_scratch, const uint32_t *dst, uint32_t stride, ObsDev *out,
+                                 uint64_t t, cudaStream_t st)
+{
+    const uint32_t nch = obs_batch_chunks(L);
+    ObsChunk *chunks = reinterpret_cast<ObsChunk *>(chunk_scratch);
+    k_obs_rows_batch<<<n_lat * nch, 32 * kObsRowsWarps, 0, st>>>(base, off, L, nch, chunks);
+    k_obs_final_batch<<<(n_lat * 32 + 255) / 256, 256, 0, st>>>(chunks, nch, n_lat, L, t, dst, stride, out);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+size_t obs_batch_scratch_bytes(uint32_t n_lat, uint32_t L)
+{
+    return (size_t)n_lat * obs_batch_chunks(L) * sizeof(ObsChunk);
 }
 
 int obs_partials(uint32_t L)

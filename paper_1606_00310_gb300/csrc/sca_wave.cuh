@@ -87,10 +87,21 @@ __device__ __forceinline__ void wave_st(uint32_t *p, const uint32_t (&r)[V])
     else *p = r[0];
 }
 
+// Philox key sources: the rule's precomputed round keys (one lattice per launch, kernel
+// parameters) or a key pair per lane group (many lattices per warp), schedule computed inline.
+struct KeysRk {
+    const uint32_t *rk;
+    __device__ __forceinline__ Ctr4 operator()(Ctr4 c) const { return philox4x32_10_rk(c, rk); }
+};
+struct KeysLane {
+    uint32_t k0, k1;
+    __device__ __forceinline__ Ctr4 operator()(Ctr4 c) const { return philox4x32_10(c, k0, k1); }
+};
+
 // Dyadic xi words (Sec. III construction, as xi_dyadic) for V words starting at word unit u0,
 // where u0 is a multiple of 4 when V == 4 (one Philox call per draw gives all four words).
-template <int V>
-__device__ __forceinline__ void wave_xi(const Rule &R, uint64_t u0, uint64_t t, int s, uint32_t (&xp)[V],
+template <int V, class KEYS>
+__device__ __forceinline__ void wave_xi(const Rule &R, const KEYS &key, uint64_t u0, uint64_t t, int s, uint32_t (&xp)[V],
                                         uint32_t (&xq)[V])
 {
 #pragma unroll
@@ -102,13 +113,13 @@ __device__ __forceinline__ void wave_xi(const Rule &R, uint64_t u0, uint64_t t, 
     for (int i = (int)R.n_draws; i >= 1; --i) {
         uint32_t r[V];
         if constexpr (V == 4) {
-            const Ctr4 o = philox4x32_10_rk(draw_counter(u0 >> 2, t, s, i, 0), R.rk);
+            const Ctr4 o = key(draw_counter(u0 >> 2, t, s, i, 0));
             r[0] = o.x; r[1 % V] = o.y; r[2 % V] = o.z; r[3 % V] = o.w;
         } else {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const uint64_t u = u0 + v;
-                r[v] = lane_of(philox4x32_10_rk(draw_counter(u >> 2, t, s, i, 0), R.rk), (uint32_t)(u & 3));
+                r[v] = lane_of(key(draw_counter(u >> 2, t, s, i, 0)), (uint32_t)(u & 3));
             }
         }
         if (i <= (int)R.np) {
@@ -129,8 +140,8 @@ __device__ __forceinline__ void wave_xi(const Rule &R, uint64_t u0, uint64_t t, 
 // The same construction with the number of draws ND fixed at compile time, so the ND Philox
 // chains are independent straight-line code the scheduler interleaves; DP / DQ false when
 // p / q is exactly 0 (that word is then 0 and its test drops out of the update).
-template <int V, int ND, bool DP, bool DQ>
-__device__ __forceinline__ void wave_xi_fixed(const Rule &R, uint64_t u0, uint64_t t, int s,
+template <int V, int ND, bool DP, bool DQ, class KEYS>
+__device__ __forceinline__ void wave_xi_fixed(const Rule &R, const KEYS &key, uint64_t u0, uint64_t t, int s,
                                               uint32_t (&xp)[V], uint32_t (&xq)[V])
 {
 #pragma unroll
@@ -142,13 +153,13 @@ __device__ __forceinline__ void wave_xi_fixed(const Rule &R, uint64_t u0, uint64
     for (int i = ND; i >= 1; --i) {
         uint32_t r[V];
         if constexpr (V == 4) {
-            const Ctr4 o = philox4x32_10_rk(draw_counter(u0 >> 2, t, s, i, 0), R.rk);
+            const Ctr4 o = key(draw_counter(u0 >> 2, t, s, i, 0));
             r[0] = o.x; r[1 % V] = o.y; r[2 % V] = o.z; r[3 % V] = o.w;
         } else {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const uint64_t u = u0 + v;
-                r[v] = lane_of(philox4x32_10_rk(draw_counter(u >> 2, t, s, i, 0), R.rk), (uint32_t)(u & 3));
+                r[v] = lane_of(key(draw_counter(u >> 2, t, s, i, 0)), (uint32_t)(u & 3));
             }
         }
         if (DP && i <= (int)R.np) {
@@ -307,10 +318,11 @@ __global__ void __launch_bounds__(32 * kWaveWarps) k_wave(const WaveArgs a)
                 uint32_t xp[V], xq[V];
                 if constexpr (MODE == 1) {
                     const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
+                    const KeysRk key{a.R.rk};
                     if constexpr (ND == 0)
-                        wave_xi<V>(a.R, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
+                        wave_xi<V>(a.R, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
                     else
-                        wave_xi_fixed<V, ND, DP, DQ>(a.R, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1),
+                        wave_xi_fixed<V, ND, DP, DQ>(a.R, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1),
                                                      s, xp, xq);
                 }
 #pragma unroll

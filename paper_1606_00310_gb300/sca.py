@@ -62,6 +62,8 @@ SIGNATURES = {
     "sca_set_fused_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "sca_set_temporal_block": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_set_wave_bands": (C.c_int, [C.c_void_p, C.c_int]),
+    "sca_batch_set_engine": (C.c_int, [C.c_void_p, C.c_int]),
+    "sca_batch_get_engine": (C.c_int, [C.c_void_p]),
     "sca_set_state_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint64]),
     "sca_get_state_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "sca_run_async": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.c_uint32]),
@@ -363,6 +365,12 @@ class Batch:
 
     def set_shape(self, cluster: int, threads: int):
         check(load().sca_batch_set_shape(self._h, int(cluster), int(threads)), "sca_batch_set_shape")
+
+    def set_engine(self, engine: int):
+        check(load().sca_batch_set_engine(self._h, int(engine)), "sca_batch_set_engine")
+
+    def engine(self) -> int:
+        return int(load().sca_batch_get_engine(self._h))
 
     def tune(self, probe_mcs: int = 32):
         c, t = C.c_int(), C.c_int()

@@ -140,3 +140,65 @@ def test_ensemble_config_sample(sca):
         assert np.array_equal(words[i], w_o), i
     assert len(w2) == len(times) and all(np.isfinite(w2))
     del flat128
+
+
+# Streaming engine (lane groups holding whole rows, bands streamed through registers): every
+# power-of-two size the batch takes, every {0, 1} rule, dyadic rules with 1..4 draws, q = 0
+# and not, p = 1 with dyadic q, p = 0; two runs in a row so the second starts mid-way.
+STREAM_MIX = [
+    dict(L=128, p=1.0, q=0.0, seed=21), dict(L=128, p=0.0, q=1.0, seed=22),
+    dict(L=256, p=1.0, q=1.0, seed=23), dict(L=512, p=0.5, q=0.0, seed=24),
+    dict(L=1024, p=0.75, q=0.25, seed=25), dict(L=2048, p=0.875, q=0.125, seed=26),
+    dict(L=128, p=0.9375, q=0.0625, seed=27), dict(L=256, p=1.0, q=0.25, seed=28),
+    dict(L=512, p=0.0, q=0.5, seed=29), dict(L=2048, p=1.0, q=0.0, seed=30),
+    dict(L=256, p=0.625, q=0.375, seed=31), dict(L=1024, p=0.5, q=0.5, seed=32),
+    dict(L=128, p=0.75, q=0.25, seed=33), dict(L=128, p=0.75, q=0.25, seed=34),
+]
+
+
+def _run_engine(sca, lattices, engine, runs):
+    with sca.Batch(lattices) as b:
+        b.set_engine(engine)
+        assert b.engine() == engine
+        out = []
+        for times in runs:
+            obs, ens = b.run(times)
+            out.append(([[(x.S1, x.S2, x.num, x.status) for x in obs[i]] for i in range(len(lattices))], ens))
+        words = [b.get_state(i) for i in range(len(lattices))]
+    return out, words
+
+
+def test_streaming_engine_equals_cluster_engine(sca):
+    runs = [[1, 2, 5, 9, 16], [17, 25, 40]]
+    a, wa = _run_engine(sca, STREAM_MIX, 1, runs)
+    b, wb = _run_engine(sca, STREAM_MIX, 2, runs)
+    for (oa, ea), (ob, eb) in zip(a, b):
+        assert oa == ob
+        assert ea == eb
+    for x, y in zip(wa, wb):
+        assert np.array_equal(x, y)
+
+
+def test_streaming_engine_matches_oracle(sca):
+    sub = [STREAM_MIX[i] for i in (1, 3, 4, 7, 10)]
+    times = [1, 3, 8, 11]
+    out, words = _run_engine(sca, sub, 2, [times])
+    for i, d in enumerate(sub):
+        w_o, ora = oracle_lattice(d, times)
+        assert [(r["S1"], r["S2"], r["num"], 0) for r in ora] == out[0][0][i], d
+        assert np.array_equal(words[i], w_o), d
+
+
+def test_engine_choice(sca):
+    """Per-site uniform draws and row lengths that are not a power of two keep the cluster
+    engine; asking for the streaming engine there is refused."""
+    with sca.Batch([dict(L=256, p=0.7, q=0.3, seed=1), dict(L=128, p=1.0, q=0.0, seed=2)]) as b:
+        assert b.engine() == 1
+        with pytest.raises(sca.ScaError):
+            b.set_engine(2)
+    with sca.Batch([dict(L=192, p=1.0, q=0.0, seed=1)]) as b:
+        assert b.engine() == 1
+    with sca.Batch([dict(L=256, p=0.75, q=0.25, seed=1), dict(L=512, p=1.0, q=0.0, seed=2)]) as b:
+        assert b.engine() == 2
+        with pytest.raises(sca.ScaError):
+            b.set_engine(3)
