@@ -286,10 +286,12 @@ def run_batch_only(a):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         shape = b.shape()
+        engine = b.engine()
     sites = sum(d["L"] ** 2 for d in ens)
     print(json.dumps({"metric": METRIC, "value": sites * a.batch_mcs / (ms / 1000.0), "unit": UNIT,
                       "workload": "batched ensemble, first %d lattices, %d MCS" % (len(ens), a.batch_mcs),
-                      "ms": ms, "shape": shape, "ensemble_w2_final": w2[-1]}), flush=True)
+                      "ms": ms, "engine": engine, "cluster_shape": shape,
+                      "ensemble_w2_final": w2[-1]}), flush=True)
 
 
 def run_serving(n_requests, slots):
@@ -357,6 +359,7 @@ def run_batched(sca, torch, stream, dev, L_single, peak):
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1)
         shape = b.shape()
+        engine = b.engine()
     rate = sites * 4096 / (ms / 1000.0)
     # single-lattice rates for the same two rules at L = 65536
     single = {}
@@ -379,7 +382,9 @@ def run_batched(sca, torch, stream, dev, L_single, peak):
             "single_lattice_rate_same_mix": mix,
             "single_lattice_rates": {"p=1,q=0": single[(1.0, 0.0)],
                                      "p=7/8,q=1/8": single[(0.875, 0.125)]},
-            "ratio_to_single": rate / mix, "shape": shape, "tuned": [c, t],
+            "ratio_to_single": rate / mix,
+            "engine": {1: "clusters (shared memory)", 2: "streaming (register wavefront)"}.get(engine, engine),
+            "cluster_shape": shape, "tuned": [c, t],
             "ensemble_w2_final": w2[-1]}
 
 
