@@ -218,7 +218,6 @@ int sca_set_kernel(sca_sim *s, int kernel)
             return fail(SCA_EINVAL, "temporal blocking does not fit this lattice size");
     }
     if (kernel == 4) {
-        if (s->R.mode == 2) return fail(SCA_EINVAL, "the wavefront kernel takes dyadic draws only");
         if (!wave_supported(s->L, (uint32_t)wave_max_k((int)s->R.mode), (int)s->R.mode))
             return fail(SCA_EINVAL, "the wavefront kernel does not fit this lattice size");
     }
@@ -268,6 +267,7 @@ int sca_set_temporal_block(sca_sim *s, int mcs_per_launch)
 static uint32_t wave_default_k(uint32_t L, const Rule &R)
 {
     if (R.mode == 0) return L >= 16384 ? 16u : 8u;
+    if (R.mode == 2) return 2u;
     return R.n_draws >= 3 ? 1u : 2u;
 }
 

@@ -8,6 +8,9 @@ namespace sca {
 // Dyadic instantiations (other translation unit, compiled in parallel); V words per lane.
 cudaError_t launch_wave_dyadic(const WaveArgs &a, int K, int V, int grid, cudaStream_t st);
 int wave_dyadic_blocks_per_sm(const Rule &R, int K, int V);
+// Per-site uniform instantiations (sca_wave_uniform.cu), one word per lane.
+cudaError_t launch_wave_uniform(const WaveArgs &a, int K, int grid, cudaStream_t st);
+int wave_uniform_blocks_per_sm(int K);
 
 // Words per lane: dyadic draws take four (one Philox call per draw for the four words) when
 // the row length allows, else one; {0, 1} probabilities one.
@@ -47,7 +50,7 @@ static cudaError_t launch_mode0(const WaveArgs &a, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-int wave_max_k(int mode) { return mode == 0 ? 16 : mode == 1 ? 2 : 0; }
+int wave_max_k(int mode) { return mode == 0 ? 16 : mode == 1 ? 2 : mode == 2 ? 2 : 0; }
 
 uint32_t wave_pick_k(uint32_t want, int mode)
 {
@@ -60,6 +63,7 @@ uint32_t wave_pick_k(uint32_t want, int mode)
 static int blocks_for(int K, int V, const Rule &R)
 {
     if (R.mode == 1) return wave_dyadic_blocks_per_sm(R, K, V);
+    if (R.mode == 2) return wave_uniform_blocks_per_sm(K);
     const bool dp = R.Pp != 0, dq = R.Pq != 0;
     switch (K) {
     case 1: return blocks_mode0<1>(dp, dq);
@@ -112,6 +116,7 @@ cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t
     const int grid = (int)((tiles + kWaveWarps - 1) / kWaveWarps);
     count_launches(1);
     if (mode == 1) return launch_wave_dyadic(a, (int)k, V, grid, st);
+    if (mode == 2) return launch_wave_uniform(a, (int)k, grid, st);
     switch (k) {
     case 1: return launch_mode0<1>(a, grid, st);
     case 2: return launch_mode0<2>(a, grid, st);

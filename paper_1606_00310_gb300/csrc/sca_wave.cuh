@@ -186,7 +186,7 @@ __device__ __forceinline__ void wave_xi_fixed(const Rule &R, const KEYS &key, ui
 // of V).  U rows per loop iteration: the loop body holds U x 2K half-step updates, and the row
 // window (2K+1+U slots) shifts by U slots per iteration.  MODE 0: p, q in {0, 1} with
 // DP = (p == 1), DQ = (q == 1); MODE 1: dyadic draws, ND of them fixed at compile time (0: the
-// rule's count at run time), DP / DQ = (p != 0) / (q != 0).
+// rule's count at run time), DP / DQ = (p != 0) / (q != 0); MODE 2: per-site uniforms.
 template <int K, int V, int U, int MODE, bool DP, bool DQ, int ND = 0>
 __global__ void __launch_bounds__(32 * kWaveWarps) k_wave(const WaveArgs a)
 {
@@ -316,6 +316,14 @@ __global__ void __launch_bounds__(32 * kWaveWarps) k_wave(const WaveArgs a)
                         side[v] = __funnelshift_l(v ? mid[(v + V - 1) % V] : pv, mid[v], 1);
                 }
                 uint32_t xp[V], xq[V];
+                if constexpr (MODE == 2) {
+                    // one 32-bit uniform per site (Sec. II.B), four sites per Philox call
+                    const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        xi_uniform_word(a.R, a.R.rk, (uint64_t)y * (L / 2) + 32u * (j + v),
+                                        t0 + (uint32_t)((i - 1) >> 1), s, 0u, xp[v], xq[v]);
+                }
                 if constexpr (MODE == 1) {
                     const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
                     const KeysRk key{a.R.rk};

@@ -104,10 +104,24 @@ def test_wave_full_size_p1_closed_form(sca):
     assert all(4 * g.num == g.N ** 2 for g in obs)
 
 
+@pytest.mark.parametrize("L,p,q,k", [(256, 0.7, 0.3, 2), (320, 0.9, 0.05, 1), (4096, 0.55, 0.45, 2),
+                                     (2048, 0.3, 0.0, 2), (1984, 1.0, 0.6, 1)])
+def test_wave_uniform_equals_two_pass(sca, L, p, q, k):
+    """Per-site uniform draws (non-dyadic p, q) in the wavefront kernel."""
+    times = sorted({1, 3, k + 1, 2 * k + 3, 12})
+    res = []
+    for kernel in (sca.KERNEL_TWO_PASS, sca.KERNEL_WAVE):
+        with sca.Sim(L, seed=19, p=p, q=q, rng=sca.RNG_UNIFORM32) as sim:
+            sim.set_kernel(kernel)
+            if kernel == sca.KERNEL_WAVE:
+                sim.set_temporal_block(k)
+            obs = sim.run(times)
+            res.append(([(g.S1, g.S2, g.num) for g in obs], sim.get_state()))
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1])
+
+
 def test_wave_rejects_what_it_cannot_run(sca):
-    with sca.Sim(256, seed=1, p=0.7, q=0.3, rng=sca.RNG_UNIFORM32) as sim:
-        with pytest.raises(sca.ScaError):
-            sim.set_kernel(sca.KERNEL_WAVE)
     with sca.Sim(256, seed=1, p=0.75, q=0.25) as sim:
         sim.set_kernel(sca.KERNEL_WAVE)
         with pytest.raises(sca.ScaError):
