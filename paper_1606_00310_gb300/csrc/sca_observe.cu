@@ -35,7 +35,8 @@ __device__ __forceinline__ int64_t warp_sum(int64_t v)
 
 // Table over the 256 values of (4 even-x bits, 4 odd-x bits): for the 8 sites in x order
 // (e0, o0, e1, o1, ...), slopes s = 2b - 1, running offsets d_k = s_0 + ... + s_k:
-// bits 0-4: sum s + 8, bits 5-11: sum d + 36, bits 12-19: sum d^2.
+// bits 0-7: sum s + 8 (<= 16), bits 8-17: sum d + 36 (<= 72), bits 18-28: sum d^2 (<= 204).
+// The fields are wide enough that eight entries add without carrying into each other.
 __device__ __forceinline__ uint32_t nibble_pair_entry(uint32_t i)
 {
     int d = 0, sd = 0, sd2 = 0;
@@ -47,27 +48,43 @@ __device__ __forceinline__ uint32_t nibble_pair_entry(uint32_t i)
         sd += d;
         sd2 += d * d;
     }
-    return (uint32_t)(d + 8) | ((uint32_t)(sd + 36) << 5) | ((uint32_t)sd2 << 12);
+    return (uint32_t)(d + 8) | ((uint32_t)(sd + 36) << 8) | ((uint32_t)sd2 << 18);
 }
 
 // 32 sites of the even-x word e and the odd-x word o (x order e0, o0, e1, o1, ...), appended
 // to a chunk whose running offset is d: sd += sum of offsets, sd2 += sum of squared offsets.
-// A block of 8 sites with table entry (S, A, B) after offset D adds 8D + A, 8D^2 + 2DA + B.
+// With the 8-site blocks' entries (S_k, A_k, B_k) and dl_k the offset inside the pair before
+// block k, the pair adds 64 d + 8 sum dl + sum A to sd and
+// 64 d^2 + 16 d sum dl + 8 sum dl^2 + 2 d sum A + 2 sum dl A + sum B to sd2; the sums of the
+// entries come from one packed addition, only the dl terms need per-block work.
 // tab: the table replicated per lane, entry i of lane l at tab[32 i + l], so the 32 lanes of a
 // warp always read 32 different banks.
 __device__ __forceinline__ void obs_word_pair(const uint32_t *tab, uint32_t e, uint32_t o, int32_t &d,
                                               int32_t &sd, int64_t &sd2)
 {
+    // byte m of x0 indexes block 2m (nibble 2m of e and of o), byte m of x1 block 2m + 1
+    const uint32_t x0 = (e & 0x0F0F0F0Fu) | ((o << 4) & 0xF0F0F0F0u);
+    const uint32_t x1 = ((e >> 4) & 0x0F0F0F0Fu) | (o & 0xF0F0F0F0u);
+    uint32_t packed = 0;
+    int32_t dl = 0, sdl = 0, sdl2 = 0, sdla = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const uint32_t ent = tab[32u * (((e >> (4 * k)) & 0xFu) | (((o >> (4 * k)) & 0xFu) << 4))];
-        const int32_t S = (int32_t)(ent & 31u) - 8;
-        const int32_t A = (int32_t)((ent >> 5) & 127u) - 36;
-        const int32_t B = (int32_t)(ent >> 12);
-        sd += 8 * d + A;
-        sd2 += (int64_t)(8 * d * d + 2 * d * A + B);
-        d += S;
+        const uint32_t idx = ((k & 1) ? x1 : x0) >> (8 * (k >> 1)) & 0xFFu;
+        const uint32_t ent = tab[32u * idx];
+        packed += ent;
+        const int32_t A = (int32_t)((ent >> 8) & 1023u) - 36;
+        sdl += dl;
+        sdl2 += dl * dl;
+        sdla += dl * A;
+        dl += (int32_t)(ent & 255u) - 8;
     }
+    const int32_t ST = (int32_t)(packed & 255u) - 64;
+    const int32_t SA = (int32_t)((packed >> 8) & 1023u) - 288;
+    const int32_t SB = (int32_t)(packed >> 18);
+    const int64_t D = d;
+    sd += 64 * d + 8 * sdl + SA;
+    sd2 += 64 * D * D + 16 * D * sdl + 8 * (int64_t)sdl2 + 2 * D * SA + 2 * (int64_t)sdla + SB;
+    d += ST;
 }
 
 constexpr int kObsRowsWarps = 8;
