@@ -163,3 +163,17 @@ def test_wave_refuses_a_state_that_is_not_a_surface(sca):
         sim.reset()                       # a reset state is a surface again
         sim.set_kernel(sca.KERNEL_WAVE)
         sim.step(2)
+
+
+def test_wave_largest_lattice_p1_closed_form(sca):
+    """L = 131072 (the largest lattice, 4 GiB of packed slopes), automatic kernel choice: the
+    height-bit kernel keeps the state flat under p = 1 and the exact W^2 is 1/4 at every time."""
+    import torch
+    L = 131072
+    with sca.Sim(L, seed=3, p=1.0, q=0.0) as sim:
+        assert sim.kernel_in_use() == sca.KERNEL_WAVE
+        flat = sim.state_tensor().clone()
+        obs = sim.run([1, 3, 20])
+        assert torch.equal(sim.state_tensor(), flat)
+        del flat
+    assert all(4 * g.num == g.N ** 2 and g.status == 0 for g in obs)
