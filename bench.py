@@ -213,11 +213,13 @@ def aggregate_replicas(local_updates, local_seconds, dist=None, device=None):
 
 
 # ----------------------------------------------------------------------------- oracle arm
-def oracle_sample(L, p, q, seconds, seed=1):
+def oracle_sample(L, p, q, seconds, seed=1, threads=0):
     """Time the CPU oracle on a band of rows of the same lattice (full width L), enough MCS
-    for about `seconds` of work.  Returns (updates_per_s, cores, description)."""
+    for about `seconds` of work, on all host cores (or `threads`).  Returns (updates_per_s,
+    cores, description)."""
     import oracle as o
-    cores = o.threads()
+    all_cores = o.threads()
+    cores = o.threads(threads) if threads else all_cores
     nrows = 16
     gx, gy = o.init_flat_band(L, 0, nrows)
     t0 = time.perf_counter()
@@ -231,6 +233,8 @@ def oracle_sample(L, p, q, seconds, seed=1):
     updates = (nrows - 1) * L * n
     desc = ("oracle (scalar, one site at a time) on a %d-row band of the L=%d lattice, "
             "p=%g q=%g, %d MCS = %.3g site updates in %.1f s" % (nrows, L, p, q, n, updates, dt))
+    if threads:
+        o.threads(all_cores)
     return updates / dt, cores, desc
 
 
@@ -419,6 +423,12 @@ def run_ours(a, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
+    # measured logic-instruction rate (roofline context for the height-bit kernel), outside
+    # the timed region
+    try:
+        logic_rate = sca.measure_logic_rate()
+    except Exception:
+        logic_rate = None
     for _ in range(a.warmup):
         step()
     vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
@@ -461,6 +471,12 @@ def run_ours(a, rank, world, local_rank):
                 "peak_source": "derived: %d SMs x %d logic lanes/clk x %.0f MHz (max SM clock)"
                                % (n_sm, ALU_LANES_PER_SM, mhz),
                 "alg_ops_per_update": WAVE_ALU_OPS_PER_UPDATE,
+                "peak_measured": logic_rate / 1e12 if logic_rate else None,
+                "frac_of_measured": achieved / (logic_rate / 1e12) if logic_rate else None,
+                "peak_measured_source": "sca_measure_logic_rate: independent LOP3 chains on "
+                                        "every SM, CUDA events",
+                "one_pass_hbm_roofline_updates_per_s": peak * 1e9 / BYTES_PER_UPDATE,
+                "x_one_pass_hbm_roofline": (upd_total / upd_s) / (peak * 1e9 / BYTES_PER_UPDATE),
                 "avg_launch_ms": avg_launch_s * 1e3, "launches": upd_launches,
                 "mcs_per_launch_avg": a.mcs * a.steps / max(1, upd_launches),
                 "hbm_GBs_state_once_per_launch": 2 * state_bytes * upd_launches / upd_s / 1e9,
@@ -586,7 +602,9 @@ def run_ours(a, rank, world, local_rank):
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
         r, cores, desc = oracle_sample(L, a.p, a.q, a.cpu_seconds)
-        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        r1, _, desc1 = oracle_sample(L, a.p, a.q, max(1.0, a.cpu_seconds / 3), threads=1)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "value_1_core": r1, "sample_1_core": desc1}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

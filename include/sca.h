@@ -371,6 +371,12 @@ const char *sca_last_error(void);   /* detail of the last failure on this thread
  * any other result means the timeout path is broken.  No trap, no fault, no unbounded spin. */
 int sca_selftest_wait_timeout(uint32_t limit_us);
 
+/* Measured issue rate of 32-bit three-input logic instructions on the current GPU, in
+ * instructions per second over the whole device: one launch of independent LOP3 chains that
+ * fills every SM, timed with CUDA events on a private stream (about 20 ms).  The denominator of
+ * the height-bit update's ALU roofline.  Errors: SCA_EINVAL, SCA_ECUDA. */
+int sca_measure_logic_rate(double *ops_per_s);
+
 /* Number of kernels this library has launched in this process (all objects, all streams). */
 uint64_t sca_kernel_launches(void);
 

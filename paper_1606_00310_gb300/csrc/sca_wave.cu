@@ -1,6 +1,7 @@
 // Register-wavefront temporal blocking: host side, {0, 1}-probability instantiations and the
 // surface check the height-bit representation relies on (kernel in sca_wave.cuh; dyadic
 // instantiations in sca_wave_dyadic.cu).
+#include "sca.h"
 #include "sca_wave.cuh"
 
 namespace sca {
@@ -197,3 +198,63 @@ cudaError_t surface_check(const uint32_t *A, uint32_t L, uint32_t *scratch, cuda
 }
 
 }  // namespace sca
+
+// ------------------------------------------------------------------------- logic-rate probe
+// Issue rate of 32-bit three-input logic instructions (the unit the height-bit update is bound
+// by) on this GPU: every thread runs eight independent LOP3 chains, every SM is filled.
+namespace sca {
+
+__global__ void __launch_bounds__(256) k_logic_rate(uint32_t iters, uint32_t seed, uint32_t *sink)
+{
+    uint32_t a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = seed * (threadIdx.x + 1u) + (uint32_t)k;
+    const uint32_t b = seed ^ threadIdx.x, c = ~seed + blockIdx.x;
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) asm("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a[k]) : "r"(b), "r"(c));
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x ^= a[k];
+    if (x == 0x9E3779B9u) *sink = x;      // keeps the chains live; practically never taken
+}
+
+}  // namespace sca
+
+extern "C" int sca_measure_logic_rate(double *ops_per_s)
+{
+    using namespace sca;
+    if (!ops_per_s) return fail(SCA_EINVAL, "NULL argument");
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    uint32_t *sink = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(uint32_t));
+    const uint32_t blocks = (uint32_t)sm_count() * 8u, threads = 256u, iters = 20000u;
+    float ms = 0.f;
+    if (e == cudaSuccess) {
+        k_logic_rate<<<blocks, threads, 0, st>>>(200u, 0x1234567u, sink);     // warm-up
+        count_launches(1);
+        e = cudaEventRecord(e0, st);
+    }
+    if (e == cudaSuccess) {
+        k_logic_rate<<<blocks, threads, 0, st>>>(iters, 0x7654321u, sink);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (sink) cudaFree(sink);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return cuda_fail(e, "logic-rate probe");
+    *ops_per_s = (double)blocks * threads * iters * 128.0 / (ms * 1e-3);
+    return SCA_OK;
+}

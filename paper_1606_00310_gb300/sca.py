@@ -62,6 +62,7 @@ SIGNATURES = {
     "sca_set_fused_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "sca_set_temporal_block": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_set_wave_bands": (C.c_int, [C.c_void_p, C.c_int]),
+    "sca_measure_logic_rate": (C.c_int, [C.POINTER(C.c_double)]),
     "sca_batch_set_engine": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_batch_get_engine": (C.c_int, [C.c_void_p]),
     "sca_set_state_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint64]),
@@ -137,6 +138,13 @@ def check(code, where):
 
 def workspace_bytes(L: int) -> int:
     return int(load().sca_workspace_bytes(L))
+
+
+def measure_logic_rate() -> float:
+    """Measured 32-bit three-input logic instructions per second of the current GPU."""
+    r = C.c_double()
+    check(load().sca_measure_logic_rate(C.byref(r)), "sca_measure_logic_rate")
+    return float(r.value)
 
 
 def kernel_launches() -> int:
