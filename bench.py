@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--only", default="", choices=["", "batch", "serve"],
                     help="run only the batched ensemble (--batch-count/--batch-mcs) or the "
                          "serving stream (--serve-requests)")
+    ap.add_argument("--batch-engine", type=int, default=0, choices=[0, 1, 2],
+                    help="with --only batch: 0 automatic, 1 clusters, 2 streaming")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-slots", type=int, default=96)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving line")
@@ -279,6 +281,8 @@ def run_batch_only(a):
     times = workloads.log_times(a.batch_mcs)
     stream = torch.cuda.Stream()
     with sca.Batch(ens, stream=stream) as b:
+        if a.batch_engine:
+            b.set_engine(a.batch_engine)
         b.run(times, want_obs=False)
         b.reset()
         torch.cuda.synchronize()
