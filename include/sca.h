@@ -142,7 +142,7 @@ int sca_set_state(sca_sim *sim, const uint32_t *host_words, size_t n_words, uint
  * (pinned memory makes the copies asynchronous; pageable memory works but copies in place).
  *
  * sca_set_state_async: as sca_set_state (same words, same t), including the surface check,
- * whose verdict the next call that chooses a kernel collects (it waits for the copy and the
+ * whose result the next call that chooses a kernel collects (it waits for the copy and the
  * check to finish).  Errors: SCA_EINVAL, SCA_ECUDA.
  * sca_get_state_async: as sca_get_state, without the synchronisation.  Errors: SCA_EINVAL,
  * SCA_ECUDA.

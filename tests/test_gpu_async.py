@@ -73,7 +73,7 @@ def test_pipelined_pair_equals_synchronous(env, L, p, q):
 
 
 def test_async_load_of_a_non_surface_is_caught(env):
-    """The surface verdict of an asynchronous load is collected before the next kernel choice:
+    """The surface check of an asynchronous load is collected before the next kernel choice:
     forcing the height-bit kernel on a broken state fails with SCA_ESTATE."""
     sca, torch = env
     L = 256
