@@ -315,3 +315,20 @@ def test_temporal_blocking_against_oracle(sca):
     words_o, ora = oracle_run_obs(L, seed, p, q, times)
     assert_obs_equal(obs, ora)
     assert np.array_equal(words, words_o)
+
+
+@pytest.mark.parametrize("kernel", [0, 4])
+def test_many_observation_times(sca, kernel):
+    """More observation times than one result block holds (records are returned 64 at a time),
+    an observation of the initial state and a repeated time, all exact against the oracle."""
+    L, seed, p, q = 128, 13, 0.75, 0.25
+    times = list(range(0, 150)) + [150, 150]
+    with sca.Sim(L, seed=seed, p=p, q=q) as sim:
+        if kernel:
+            sim.set_kernel(kernel)
+        obs = sim.run(times)
+        words = sim.get_state()
+    words_o, ora = oracle_run_obs(L, seed, p, q, times)
+    assert [g.t for g in obs] == times
+    assert_obs_equal(obs, ora)
+    assert np.array_equal(words, words_o)
