@@ -41,7 +41,11 @@ struct WaveArgs {
     Rule R;
 };
 
-constexpr int kWaveWarps = 4;          // warps (independent tiles) per CTA
+// Warps (independent tiles) per CTA: one.  The register file then fills warp by warp rather
+// than four warps at a time, and with a 32-thread launch bound the compiler fits the 16-MCS
+// {0, 1}-probability instantiation in 128 registers (16 warps per SM) where 128-thread CTAs got
+// 150 (12 warps per SM).
+constexpr int kWaveWarps = 1;
 constexpr uint32_t kWaveTileWords = 30; // words a warp tile owns (32 lanes minus two halos)
 // Rows per loop iteration (even): larger blocks shift the row window less often, smaller ones
 // keep the unrolled loop inside the instruction cache; the dyadic update carries a Philox

@@ -24,7 +24,9 @@ struct WBArgs {
     Rule R;             // class rule; the keys come from the items
 };
 
-constexpr int kWBWarps = 4;
+// One warp per CTA: the register file fills warp by warp (at 152 registers a thread 13 warps fit
+// an SM, against 12 in 128-thread CTAs).
+constexpr int kWBWarps = 1;
 
 template <int K, int V, int U, int MODE, bool DP, bool DQ, int ND>
 __global__ void __launch_bounds__(32 * kWBWarps) k_wave_batch(const WBArgs a)
