@@ -23,7 +23,7 @@ static int blocks_per_sm()
     static int n = 0;
     if (n == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wave<K, 1, kWaveU0, 0, DP, DQ>, 32 * kWaveWarps, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wave01_kernel<K, DP, DQ>(), 32 * kWaveWarps, 0) !=
                 cudaSuccess || b <= 0)
             b = 1;
         n = b;
@@ -44,10 +44,10 @@ template <int K>
 static cudaError_t launch_mode0(const WaveArgs &a, int grid, cudaStream_t st)
 {
     const bool dp = a.R.Pp != 0, dq = a.R.Pq != 0;
-    if (dp && dq) k_wave<K, 1, kWaveU0, 0, true, true><<<grid, 32 * kWaveWarps, 0, st>>>(a);
-    else if (dp) k_wave<K, 1, kWaveU0, 0, true, false><<<grid, 32 * kWaveWarps, 0, st>>>(a);
-    else if (dq) k_wave<K, 1, kWaveU0, 0, false, true><<<grid, 32 * kWaveWarps, 0, st>>>(a);
-    else k_wave<K, 1, kWaveU0, 0, false, false><<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    if (dp && dq) wave01_kernel<K, true, true>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else if (dp) wave01_kernel<K, true, false>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else if (dq) wave01_kernel<K, false, true>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else wave01_kernel<K, false, false>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
     return cudaGetLastError();
 }
 

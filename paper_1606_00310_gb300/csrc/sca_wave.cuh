@@ -16,10 +16,11 @@
 //
 // Wavefront.  Half-step i at row r needs half-step i-1 at rows r-1, r, r+1, so one warp
 // streams a band of rows: when row R arrives, half-step 1 runs on row R-1, ..., half-step 2K
-// on row R-2K, and row R-2K is final for all K MCS.  The 2K+2 live rows stay in registers; the
-// loop is unrolled by the window length so every row slot is a fixed register, and because the
-// half-step index and the row advance together, all half-steps of one position agree on which
-// side the shifted x-neighbour word comes from (a compile-time fact after unrolling).
+// on row R-2K, and row R-2K is final for all K MCS.  The live rows stay in registers: the row
+// loop is unrolled by a block of U rows, so every row slot is a fixed register, and the window
+// slides by U slots after each block.  Because the half-step index and the row advance
+// together, all half-steps of one position agree on which side the shifted x-neighbour word
+// comes from (a compile-time fact after unrolling).
 //
 // Tiles.  Lane l of a warp owns one packed word of every row of its band; lanes 0 and 31 hold
 // halo words (the x light cone grows by at most one bit per half-step, so one word on each side
@@ -56,8 +57,19 @@ constexpr uint32_t kWaveTileWords = 30; // words a warp tile owns (32 lanes minu
 #ifndef SCA_WAVE_U1
 #define SCA_WAVE_U1 2
 #endif
+#ifndef SCA_WAVE_MINB
+#define SCA_WAVE_MINB 16
+#endif
 constexpr int kWaveU0 = SCA_WAVE_U0;   // {0, 1} probabilities
 constexpr int kWaveU1 = SCA_WAVE_U1;   // dyadic draws
+
+// Resident CTAs per SM the compiler must allow.  The 16-MCS {0, 1}-probability kernel is held to
+// 128 registers (16 warps per SM; left free it takes ~150 and 12 fit).  The others get 0, no
+// bound: even a bound of 1 changes the compiler's register choice for them.
+__host__ __device__ constexpr int wave_min_blocks(int K, int V, int MODE)
+{
+    return (MODE == 0 && V == 1 && K == 16) ? SCA_WAVE_MINB : 0;
+}
 
 __device__ __forceinline__ uint32_t wave_xor_prefix(uint32_t g)
 {
@@ -186,13 +198,176 @@ __device__ __forceinline__ void wave_xi_fixed(const Rule &R, const KEYS &key, ui
     }
 }
 
+// The 2K half-steps of the wavefront when row R arrives in slot S + 1 + u: half-step i on row
+// R - i (slot S + 1 + u - i).  yu is the lattice row of row R (used by the random draws).
+template <int K, int V, int U, int MODE, bool DP, bool DQ, int ND>
+__device__ __forceinline__ void wave_half_steps(const Rule &Rl, uint32_t (&h)[2 * K + 1 + U][2][V], const int u,
+                                                const uint32_t yu, const uint32_t L, const uint32_t W,
+                                                const uint32_t j, const uint64_t t0)
+{
+    constexpr int S = 2 * K;
+    constexpr int base = S + 1;
+    const uint32_t FULL = 0xFFFFFFFFu;
+    // rows of sublattice s at parity (s + y) & 1 == 1 sit one site right; for every half-step
+    // of this position (s + y) & 1 == (R + 1) & 1, and the first row of a block is even
+    const bool right_shift = ((u + 1) & 1) != 0;
+#pragma unroll
+    for (int i = 1; i <= S; ++i) {
+        const int s = (i - 1) & 1, ns = s ^ 1;
+        const int c = base + u - i;             // slot of row R - i
+        uint32_t(&b)[V] = h[c][s];
+        const uint32_t(&up)[V] = h[c - 1][ns];
+        const uint32_t(&dn)[V] = h[c + 1][ns];
+        const uint32_t(&mid)[V] = h[c][ns];
+        // the x-neighbour that is not in the same bit position: bit k+1 of the other
+        // sublattice when this row sits right, else bit k-1
+        uint32_t side[V];
+        if (right_shift) {
+            const uint32_t nx = __shfl_down_sync(FULL, mid[0], 1);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                side[v] = __funnelshift_r(mid[v], v + 1 < V ? mid[(v + 1) % V] : nx, 1);
+        } else {
+            const uint32_t pv = __shfl_up_sync(FULL, mid[V - 1], 1);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                side[v] = __funnelshift_l(v ? mid[(v + V - 1) % V] : pv, mid[v], 1);
+        }
+        uint32_t xp[V], xq[V];
+        if constexpr (MODE == 2) {
+            // one 32-bit uniform per site (Sec. II.B), four sites per Philox call
+            const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                xi_uniform_word(Rl, Rl.rk, (uint64_t)y * (L / 2) + 32u * (j + v), t0 + (uint32_t)((i - 1) >> 1), s,
+                                0u, xp[v], xq[v]);
+        }
+        if constexpr (MODE == 1) {
+            const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
+            const KeysRk key{Rl.rk};
+            if constexpr (ND == 0)
+                wave_xi<V>(Rl, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
+            else
+                wave_xi_fixed<V, ND, DP, DQ>(Rl, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            // e(n) = b xor b(n) for the four neighbours; local minimum: every e == s, local
+            // maximum: every e == 1 - s
+            const uint32_t e_or = (b[v] ^ up[v]) | (b[v] ^ dn[v]) | (b[v] ^ mid[v]) | (b[v] ^ side[v]);
+            const uint32_t e_and = (b[v] ^ up[v]) & (b[v] ^ dn[v]) & (b[v] ^ mid[v]) & (b[v] ^ side[v]);
+            const uint32_t is_min = s == 0 ? ~e_or : e_and;
+            const uint32_t is_max = s == 0 ? e_and : ~e_or;
+            uint32_t m;
+            if constexpr (MODE == 0) m = (DP ? is_min : 0u) | (DQ ? is_max : 0u);
+            else m = (xp[v] & is_min) | (xq[v] & is_max);
+            b[v] ^= m;
+        }
+    }
+}
+
+// Store a final row (height bits hr, the row above hp) as its four canonical slope words at
+// word offset o: sy-bit = b xor b(x, y-1) xor s and sx-bit = b xor b(x-1, y) xor s.  In even
+// rows sublattice 0 sits at even x, so its left neighbour is bit k-1 of the sublattice-1 word
+// and sublattice 1's is bit k of the sublattice-0 word; odd rows (odd u) the other way round.
+template <int V>
+__device__ __forceinline__ void wave_store_row(const uint32_t (&hr)[2][V], const uint32_t (&hp)[2][V], const int u,
+                                               const bool own, const uint32_t o, uint32_t *DX0, uint32_t *DY0,
+                                               uint32_t *DX1, uint32_t *DY1)
+{
+    const int lo = (u & 1) ? 1 : 0;             // sublattice whose left neighbour is shifted
+    const uint32_t pv = __shfl_up_sync(0xFFFFFFFFu, hr[lo ^ 1][V - 1], 1);
+    uint32_t sx[2][V], sy[2][V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        sy[0][v] = hr[0][v] ^ hp[1][v];
+        sy[1][v] = ~(hr[1][v] ^ hp[0][v]);
+        const uint32_t left = __funnelshift_l(v ? hr[lo ^ 1][(v + V - 1) % V] : pv, hr[lo ^ 1][v], 1);
+        sx[lo][v] = hr[lo][v] ^ left;
+        sx[lo ^ 1][v] = hr[lo ^ 1][v] ^ hr[lo][v];
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) sx[1][v] = ~sx[1][v];
+    if (own) {
+        wave_st<V>(DX0 + o, sx[0]);
+        wave_st<V>(DY0 + o, sy[0]);
+        wave_st<V>(DX1 + o, sx[1]);
+        wave_st<V>(DY1 + o, sy[1]);
+    }
+}
+
+// b(x, y) = b(x, y-1) xor sy-bit(x, y) xor s for both sublattices of an arriving row (sites of
+// sublattice s have parity s).
+template <int V>
+__device__ __forceinline__ void wave_convert_row(uint32_t (&hn)[2][V], const uint32_t (&hp)[2][V],
+                                                 const uint32_t (&sy)[2][V])
+{
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        hn[0][v] = hp[1][v] ^ sy[0][v];
+        hn[1][v] = ~(hp[0][v] ^ sy[1][v]);
+    }
+}
+
+// Slide the row window by U slots once a block of U rows has been processed.
+template <int K, int V, int U>
+__device__ __forceinline__ void wave_slide(uint32_t (&h)[2 * K + 1 + U][2][V])
+{
+#pragma unroll
+    for (int c = 0; c <= 2 * K; ++c)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            h[c][0][v] = h[c + U][0][v];
+            h[c][1][v] = h[c + U][1][v];
+        }
+}
+
+// Per-tile values the row blocks of the {0, 1}-probability kernels share.
+struct WaveTile {
+    const uint32_t *SY0, *SY1;
+    uint32_t *DX0, *DY0, *DX1, *DY1;
+    uint32_t L, W, plane, NR, j;
+    uint32_t ol;     // word offset of the next row to load (32 bits: a plane holds <= 2^28 words)
+    uint32_t os;     // word offset of the next final row to store
+    bool own;        // this lane stores its words
+};
+
+// One block of U arriving rows R0 .. R0 + U - 1 of a {0, 1}-probability tile.  CHK: some row of
+// the block is the first one, lies past the band's end, has no row U further on to prefetch, or
+// precedes the first final row, so every per-row step is guarded; blocks in the steady state
+// skip the guards.
+template <int K, int V, int U, bool DP, bool DQ, bool CHK>
+__device__ __forceinline__ void wave_block01(const Rule &Rl, WaveTile &T, uint32_t (&h)[2 * K + 1 + U][2][V],
+                                             uint32_t (&rc)[U][2][V], const uint32_t R0)
+{
+    constexpr int S = 2 * K;
+    constexpr int base = S + 1;                 // slot of row R0
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t R = R0 + (uint32_t)u;
+        if (CHK && R >= T.NR) break;
+        if (!CHK || R > 0) wave_convert_row<V>(h[base + u], h[base + u - 1], rc[u]);
+        if (!CHK || R + U < T.NR) {             // row R + U into the ring entry just freed
+            wave_ld<V>(T.SY0 + T.ol, rc[u][0]);
+            wave_ld<V>(T.SY1 + T.ol, rc[u][1]);
+        }
+        T.ol += T.W;
+        if (T.ol >= T.plane) T.ol -= T.plane;
+        wave_half_steps<K, V, U, 0, DP, DQ, 0>(Rl, h, u, 0u, T.L, T.W, T.j, 0u);
+        if (!CHK || R >= 4u * K + 2u) {         // row R - 2K is final
+            wave_store_row<V>(h[base + u - S], h[base + u - S - 1], u, T.own, T.os, T.DX0, T.DY0, T.DX1, T.DY1);
+            T.os += T.W;
+        }
+    }
+}
+
 // V consecutive words per lane (V = 1, 2 or 4; the lattice's words per row must be a multiple
 // of V).  U rows per loop iteration: the loop body holds U x 2K half-step updates, and the row
 // window (2K+1+U slots) shifts by U slots per iteration.  MODE 0: p, q in {0, 1} with
 // DP = (p == 1), DQ = (q == 1); MODE 1: dyadic draws, ND of them fixed at compile time (0: the
 // rule's count at run time), DP / DQ = (p != 0) / (q != 0); MODE 2: per-site uniforms.
 template <int K, int V, int U, int MODE, bool DP, bool DQ, int ND = 0>
-__global__ void __launch_bounds__(32 * kWaveWarps) k_wave(const WaveArgs a)
+__global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) k_wave(const WaveArgs a)
 {
     constexpr int S = 2 * K;                    // half-steps per launch
     constexpr int NW = S + 1 + U;               // row slots: slot of row R = R - R0 + S + 1
@@ -222,7 +397,9 @@ __global__ void __launch_bounds__(32 * kWaveWarps) k_wave(const WaveArgs a)
     const bool own = lane >= 1 && lane <= 30 && jj < (int64_t)W;
 
     uint32_t h[NW][2][V];           // height bits [slot][sublattice][word]
-    uint32_t rc[U][2][V], rn[U][2][V];   // sy- words of this block's rows / the next block's
+    // sy- words of rows R .. R + U - 1 (ring: row R sits in entry R mod U; once a row has been
+    // converted its entry takes the row U further on, in flight while the block computes)
+    uint32_t rc[U][2][V];
 #pragma unroll
     for (int i = 0; i < NW; ++i)
 #pragma unroll
@@ -260,144 +437,64 @@ __global__ void __launch_bounds__(32 * kWaveWarps) k_wave(const WaveArgs a)
             h[S + 1][1][v] = pre[v] ^ flip ^ nsx1[v];
         }
     }
-    uint32_t yl = first + 1 >= L ? first + 1 - L : first + 1;     // next row to load
+    const uint32_t plane32 = L * W;
+    uint32_t ol = (first + 1 >= L ? first + 1 - L : first + 1) * W + j;     // next row to load
 #pragma unroll
     for (int u = 1; u < U; ++u) {
         if ((uint32_t)u < NR) {
-            wave_ld<V>(SY0 + (size_t)yl * W + j, rc[u][0]);
-            wave_ld<V>(SY1 + (size_t)yl * W + j, rc[u][1]);
+            wave_ld<V>(SY0 + ol, rc[u][0]);
+            wave_ld<V>(SY1 + ol, rc[u][1]);
         }
-        if (++yl == L) yl = 0;
+        ol += W;
+        if (ol >= plane32) ol -= plane32;
     }
-    uint32_t yu = first;                                          // lattice row of row R
+    uint32_t os = y0 * W + j;                   // lattice row y0 is the first final row
+    constexpr int base = S + 1;                 // slot of the first row of a block
 
-    for (uint32_t R0 = 0; R0 < NR; R0 += U) {
-        // sy- words of the next block's rows, in flight while this block computes
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (R0 + U + u < NR) {
-                wave_ld<V>(SY0 + (size_t)yl * W + j, rn[u][0]);
-                wave_ld<V>(SY1 + (size_t)yl * W + j, rn[u][1]);
-            }
-            if (++yl == L) yl = 0;
+    if constexpr (MODE == 0) {
+        WaveTile T;
+        T.SY0 = SY0; T.SY1 = SY1;
+        T.DX0 = DX0; T.DY0 = DY0; T.DX1 = DX1; T.DY1 = DY1;
+        T.L = L; T.W = W; T.plane = plane32; T.NR = NR; T.j = j;
+        T.ol = ol; T.os = os; T.own = own;
+        for (uint32_t R0 = 0; R0 < NR; R0 += U) {
+            if (R0 >= 4u * K + 2u && R0 + 2u * U <= NR)
+                wave_block01<K, V, U, DP, DQ, false>(a.R, T, h, rc, R0);
+            else
+                wave_block01<K, V, U, DP, DQ, true>(a.R, T, h, rc, R0);
+            wave_slide<K, V, U>(h);
         }
+    } else {
+        uint32_t yu = first;                    // lattice row of row R
+        for (uint32_t R0 = 0; R0 < NR; R0 += U) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t R = R0 + (uint32_t)u;
-            if (R >= NR) break;
-            constexpr int base = S + 1;             // slot of row R0
-            if (R > 0) {
-                // b(x, y) = b(x, y-1) xor sy-bit(x, y) xor s (sites of sublattice s have parity s)
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    h[base + u][0][v] = h[base + u - 1][1][v] ^ rc[u][0][v];
-                    h[base + u][1][v] = ~(h[base + u - 1][0][v] ^ rc[u][1][v]);
+            for (int u = 0; u < U; ++u) {
+                const uint32_t R = R0 + (uint32_t)u;
+                if (R >= NR) break;
+                if (R > 0) wave_convert_row<V>(h[base + u], h[base + u - 1], rc[u]);
+                if (R + U < NR) {               // row R + U into the ring entry just freed
+                    wave_ld<V>(SY0 + ol, rc[u][0]);
+                    wave_ld<V>(SY1 + ol, rc[u][1]);
                 }
+                ol += W;
+                if (ol >= plane32) ol -= plane32;
+                wave_half_steps<K, V, U, MODE, DP, DQ, ND>(a.R, h, u, yu, L, W, j, t0);
+                if (R >= 4u * K + 2u) {         // row R - 2K is final
+                    wave_store_row<V>(h[base + u - S], h[base + u - S - 1], u, own, os, DX0, DY0, DX1, DY1);
+                    os += W;
+                }
+                if (++yu == L) yu = 0;
             }
-            // rows of sublattice s at parity (s + y) & 1 == 1 sit one site right; for every
-            // half-step of this position (s + y) & 1 == (R + 1) & 1, and R0 is even
-            const bool right_shift = ((u + 1) & 1) != 0;
-#pragma unroll
-            for (int i = 1; i <= S; ++i) {
-                const int s = (i - 1) & 1, ns = s ^ 1;
-                const int c = base + u - i;         // slot of row R - i
-                uint32_t(&b)[V] = h[c][s];
-                const uint32_t(&up)[V] = h[c - 1][ns];
-                const uint32_t(&dn)[V] = h[c + 1][ns];
-                const uint32_t(&mid)[V] = h[c][ns];
-                // the x-neighbour that is not in the same bit position: bit k+1 of the other
-                // sublattice when this row sits right, else bit k-1
-                uint32_t side[V];
-                if (right_shift) {
-                    const uint32_t nx = __shfl_down_sync(FULL, mid[0], 1);
-#pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        side[v] = __funnelshift_r(mid[v], v + 1 < V ? mid[(v + 1) % V] : nx, 1);
-                } else {
-                    const uint32_t pv = __shfl_up_sync(FULL, mid[V - 1], 1);
-#pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        side[v] = __funnelshift_l(v ? mid[(v + V - 1) % V] : pv, mid[v], 1);
-                }
-                uint32_t xp[V], xq[V];
-                if constexpr (MODE == 2) {
-                    // one 32-bit uniform per site (Sec. II.B), four sites per Philox call
-                    const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
-#pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        xi_uniform_word(a.R, a.R.rk, (uint64_t)y * (L / 2) + 32u * (j + v),
-                                        t0 + (uint32_t)((i - 1) >> 1), s, 0u, xp[v], xq[v]);
-                }
-                if constexpr (MODE == 1) {
-                    const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
-                    const KeysRk key{a.R.rk};
-                    if constexpr (ND == 0)
-                        wave_xi<V>(a.R, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
-                    else
-                        wave_xi_fixed<V, ND, DP, DQ>(a.R, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1),
-                                                     s, xp, xq);
-                }
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    // e(n) = b xor b(n) for the four neighbours; local minimum: every e == s,
-                    // local maximum: every e == 1 - s
-                    const uint32_t e_or = (b[v] ^ up[v]) | (b[v] ^ dn[v]) | (b[v] ^ mid[v]) | (b[v] ^ side[v]);
-                    const uint32_t e_and = (b[v] ^ up[v]) & (b[v] ^ dn[v]) & (b[v] ^ mid[v]) & (b[v] ^ side[v]);
-                    const uint32_t is_min = s == 0 ? ~e_or : e_and;
-                    const uint32_t is_max = s == 0 ? e_and : ~e_or;
-                    uint32_t m;
-                    if constexpr (MODE == 0) m = (DP ? is_min : 0u) | (DQ ? is_max : 0u);
-                    else m = (xp[v] & is_min) | (xq[v] & is_max);
-                    b[v] ^= m;
-                }
-            }
-            if (R >= 4u * K + 2u) {                 // row R - 2K (lattice row y) is final
-                const uint32_t(&hr)[2][V] = h[base + u - S];
-                const uint32_t(&hp)[2][V] = h[base + u - S - 1];
-                const uint32_t y = y0 + R - 4u * K - 2u;
-                // sy-bit = b xor b(x, y-1) xor s and sx-bit = b xor b(x-1, y) xor s.  In even
-                // rows sublattice 0 sits at even x, so its left neighbour is bit k-1 of the
-                // sublattice-1 word and sublattice 1's is bit k of the sublattice-0 word; odd
-                // rows the other way round (y has the parity of u).
-                const int lo = (u & 1) ? 1 : 0;             // sublattice whose left neighbour is shifted
-                const uint32_t pv = __shfl_up_sync(FULL, hr[lo ^ 1][V - 1], 1);
-                uint32_t sx[2][V], sy[2][V];
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    sy[0][v] = hr[0][v] ^ hp[1][v];
-                    sy[1][v] = ~(hr[1][v] ^ hp[0][v]);
-                    const uint32_t left = __funnelshift_l(v ? hr[lo ^ 1][(v + V - 1) % V] : pv, hr[lo ^ 1][v], 1);
-                    sx[lo][v] = hr[lo][v] ^ left;
-                    sx[lo ^ 1][v] = hr[lo ^ 1][v] ^ hr[lo][v];
-                }
-#pragma unroll
-                for (int v = 0; v < V; ++v) sx[1][v] = ~sx[1][v];
-                if (own) {
-                    const size_t o = (size_t)y * W + j;
-                    wave_st<V>(DX0 + o, sx[0]);
-                    wave_st<V>(DY0 + o, sy[0]);
-                    wave_st<V>(DX1 + o, sx[1]);
-                    wave_st<V>(DY1 + o, sy[1]);
-                }
-            }
-            if (++yu == L) yu = 0;
+            wave_slide<K, V, U>(h);
         }
-        // slide the window by U rows
-#pragma unroll
-        for (int c = 0; c <= S; ++c)
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                h[c][0][v] = h[c + U][0][v];
-                h[c][1][v] = h[c + U][1][v];
-            }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                rc[u][0][v] = rn[u][0][v];
-                rc[u][1][v] = rn[u][1][v];
-            }
     }
+}
+
+// The kernel that runs K MCS per launch with {0, 1} probabilities.
+template <int K, bool DP, bool DQ>
+constexpr void (*wave01_kernel())(WaveArgs)
+{
+    return k_wave<K, 1, kWaveU0, 0, DP, DQ>;
 }
 
 }  // namespace sca
