@@ -71,6 +71,15 @@ __host__ __device__ constexpr int wave_min_blocks(int K, int V, int MODE)
     return (MODE == 0 && V == 1 && K == 16) ? SCA_WAVE_MINB : 0;
 }
 
+// Three-input bitwise function given by its truth table (bit 4a + 2b + c of LUT is f(a, b, c)).
+template <uint32_t LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+
 __device__ __forceinline__ uint32_t wave_xor_prefix(uint32_t g)
 {
     g ^= g << 1;
@@ -198,6 +207,38 @@ __device__ __forceinline__ void wave_xi_fixed(const Rule &R, const KEYS &key, ui
     }
 }
 
+// One site word after a half-step of its sublattice s (Eqs. 2 and 3 in height bits): with
+// e(n) = b xor b(n) for the four neighbours, a site is a local minimum when every e == s and a
+// local maximum when every e == 1 - s; xp / xq gate deposition / removal (MODE 0: DP / DQ).
+template <int MODE, bool DP, bool DQ>
+__device__ __forceinline__ uint32_t wave_update(uint32_t b, uint32_t up, uint32_t dn, uint32_t mid, uint32_t side,
+                                                int s, uint32_t xp, uint32_t xq)
+{
+    if constexpr (MODE == 0 && DP != DQ) {
+        // one kind of flip in three three-input operations: the flip set is "every e == 0" (the
+        // OR of the e's is 0) or "every e == 1" (their AND is 1); minima of even sites and
+        // maxima of odd sites are the first kind
+        if ((s == 0) == DP) {
+            const uint32_t t1 = lop3<0x7E>(b, up, dn);       // (b ^ up) | (b ^ dn)
+            const uint32_t t2 = lop3<0x7E>(b, mid, side);    // (b ^ mid) | (b ^ side)
+            return lop3<0xE1>(b, t1, t2);                    // b ^ ~(t1 | t2)
+        } else {
+            const uint32_t t1 = lop3<0x18>(b, up, dn);       // (b ^ up) & (b ^ dn)
+            const uint32_t t2 = lop3<0x18>(b, mid, side);    // (b ^ mid) & (b ^ side)
+            return lop3<0x78>(b, t1, t2);                    // b ^ (t1 & t2)
+        }
+    } else {
+        const uint32_t e_or = (b ^ up) | (b ^ dn) | (b ^ mid) | (b ^ side);
+        const uint32_t e_and = (b ^ up) & (b ^ dn) & (b ^ mid) & (b ^ side);
+        const uint32_t is_min = s == 0 ? ~e_or : e_and;
+        const uint32_t is_max = s == 0 ? e_and : ~e_or;
+        uint32_t m;
+        if constexpr (MODE == 0) m = (DP ? is_min : 0u) | (DQ ? is_max : 0u);
+        else m = (xp & is_min) | (xq & is_max);
+        return b ^ m;
+    }
+}
+
 // The 2K half-steps of the wavefront when row R arrives in slot S + 1 + u: half-step i on row
 // R - i (slot S + 1 + u - i).  yu is the lattice row of row R (used by the random draws).
 template <int K, int V, int U, int MODE, bool DP, bool DQ, int ND>
@@ -233,7 +274,7 @@ __device__ __forceinline__ void wave_half_steps(const Rule &Rl, uint32_t (&h)[2 
             for (int v = 0; v < V; ++v)
                 side[v] = __funnelshift_l(v ? mid[(v + V - 1) % V] : pv, mid[v], 1);
         }
-        uint32_t xp[V], xq[V];
+        uint32_t xp[V] = {}, xq[V] = {};
         if constexpr (MODE == 2) {
             // one 32-bit uniform per site (Sec. II.B), four sites per Philox call
             const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
@@ -252,16 +293,7 @@ __device__ __forceinline__ void wave_half_steps(const Rule &Rl, uint32_t (&h)[2 
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            // e(n) = b xor b(n) for the four neighbours; local minimum: every e == s, local
-            // maximum: every e == 1 - s
-            const uint32_t e_or = (b[v] ^ up[v]) | (b[v] ^ dn[v]) | (b[v] ^ mid[v]) | (b[v] ^ side[v]);
-            const uint32_t e_and = (b[v] ^ up[v]) & (b[v] ^ dn[v]) & (b[v] ^ mid[v]) & (b[v] ^ side[v]);
-            const uint32_t is_min = s == 0 ? ~e_or : e_and;
-            const uint32_t is_max = s == 0 ? e_and : ~e_or;
-            uint32_t m;
-            if constexpr (MODE == 0) m = (DP ? is_min : 0u) | (DQ ? is_max : 0u);
-            else m = (xp[v] & is_min) | (xq[v] & is_max);
-            b[v] ^= m;
+            b[v] = wave_update<MODE, DP, DQ>(b[v], up[v], dn[v], mid[v], side[v], s, xp[v], xq[v]);
         }
     }
 }

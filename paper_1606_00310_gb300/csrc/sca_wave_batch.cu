@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(32 * kWBWarps) k_wave_batch(const WBArgs a)
                     for (int v = 0; v < V; ++v)
                         side[v] = __funnelshift_l(v ? mid[(v + V - 1) % V] : pv, mid[v], 1);
                 }
-                uint32_t xp[V], xq[V];
+                uint32_t xp[V] = {}, xq[V] = {};
                 if constexpr (MODE == 1) {
                     const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
                     if constexpr (ND == 0)
@@ -163,16 +163,8 @@ __global__ void __launch_bounds__(32 * kWBWarps) k_wave_batch(const WBArgs a)
                                                      s, xp, xq);
                 }
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const uint32_t e_or = (b[v] ^ up[v]) | (b[v] ^ dn[v]) | (b[v] ^ mid[v]) | (b[v] ^ side[v]);
-                    const uint32_t e_and = (b[v] ^ up[v]) & (b[v] ^ dn[v]) & (b[v] ^ mid[v]) & (b[v] ^ side[v]);
-                    const uint32_t is_min = s == 0 ? ~e_or : e_and;
-                    const uint32_t is_max = s == 0 ? e_and : ~e_or;
-                    uint32_t m;
-                    if constexpr (MODE == 0) m = (DP ? is_min : 0u) | (DQ ? is_max : 0u);
-                    else m = (xp[v] & is_min) | (xq[v] & is_max);
-                    b[v] ^= m;
-                }
+                for (int v = 0; v < V; ++v)
+                    b[v] = wave_update<MODE, DP, DQ>(b[v], up[v], dn[v], mid[v], side[v], s, xp[v], xq[v]);
             }
             if (R >= 4u * K + 2u) {
                 const uint32_t(&hr)[2][V] = h[base + u - S];
