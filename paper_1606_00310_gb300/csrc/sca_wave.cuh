@@ -60,8 +60,16 @@ constexpr uint32_t kWaveTileWords = 30; // words a warp tile owns (32 lanes minu
 #ifndef SCA_WAVE_MINB
 #define SCA_WAVE_MINB 16
 #endif
+#ifndef SCA_WAVE_P0
+#define SCA_WAVE_P0 SCA_WAVE_U0
+#endif
 constexpr int kWaveU0 = SCA_WAVE_U0;   // {0, 1} probabilities
 constexpr int kWaveU1 = SCA_WAVE_U1;   // dyadic draws
+
+// Prefetch distance in rows (the sy- ring's entries) for U rows per block: a divisor of U, so
+// that the ring entry of every row of a block is a compile-time index.
+__host__ __device__ constexpr int wave_ring(int U, int MODE) { return MODE == 0 ? SCA_WAVE_P0 : U; }
+static_assert(SCA_WAVE_U0 % SCA_WAVE_P0 == 0, "the ring length divides the rows per block");
 
 // Resident CTAs per SM the compiler must allow.  The 16-MCS {0, 1}-probability kernel is held to
 // 128 registers (16 warps per SM; left free it takes ~150 and 12 fit).  The others get 0, no
@@ -368,9 +376,9 @@ struct WaveTile {
 // the block is the first one, lies past the band's end, has no row U further on to prefetch, or
 // precedes the first final row, so every per-row step is guarded; blocks in the steady state
 // skip the guards.
-template <int K, int V, int U, bool DP, bool DQ, bool CHK>
+template <int K, int V, int U, int P, bool DP, bool DQ, bool CHK>
 __device__ __forceinline__ void wave_block01(const Rule &Rl, WaveTile &T, uint32_t (&h)[2 * K + 1 + U][2][V],
-                                             uint32_t (&rc)[U][2][V], const uint32_t R0)
+                                             uint32_t (&rc)[P][2][V], const uint32_t R0)
 {
     constexpr int S = 2 * K;
     constexpr int base = S + 1;                 // slot of row R0
@@ -378,10 +386,10 @@ __device__ __forceinline__ void wave_block01(const Rule &Rl, WaveTile &T, uint32
     for (int u = 0; u < U; ++u) {
         const uint32_t R = R0 + (uint32_t)u;
         if (CHK && R >= T.NR) break;
-        if (!CHK || R > 0) wave_convert_row<V>(h[base + u], h[base + u - 1], rc[u]);
-        if (!CHK || R + U < T.NR) {             // row R + U into the ring entry just freed
-            wave_ld<V>(T.SY0 + T.ol, rc[u][0]);
-            wave_ld<V>(T.SY1 + T.ol, rc[u][1]);
+        if (!CHK || R > 0) wave_convert_row<V>(h[base + u], h[base + u - 1], rc[u % P]);
+        if (!CHK || R + P < T.NR) {             // row R + P into the ring entry just freed
+            wave_ld<V>(T.SY0 + T.ol, rc[u % P][0]);
+            wave_ld<V>(T.SY1 + T.ol, rc[u % P][1]);
         }
         T.ol += T.W;
         if (T.ol >= T.plane) T.ol -= T.plane;
@@ -429,9 +437,11 @@ __global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) 
     const bool own = lane >= 1 && lane <= 30 && jj < (int64_t)W;
 
     uint32_t h[NW][2][V];           // height bits [slot][sublattice][word]
-    // sy- words of rows R .. R + U - 1 (ring: row R sits in entry R mod U; once a row has been
-    // converted its entry takes the row U further on, in flight while the block computes)
-    uint32_t rc[U][2][V];
+    // sy- words of rows R .. R + P - 1 (ring: row R sits in entry R mod P; once a row has been
+    // converted its entry takes the row P further on, in flight while the next rows compute)
+    constexpr int P = wave_ring(U, MODE);
+    static_assert(U % P == 0, "the ring length divides the rows per block");
+    uint32_t rc[P][2][V];
 #pragma unroll
     for (int i = 0; i < NW; ++i)
 #pragma unroll
@@ -472,7 +482,7 @@ __global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) 
     const uint32_t plane32 = L * W;
     uint32_t ol = (first + 1 >= L ? first + 1 - L : first + 1) * W + j;     // next row to load
 #pragma unroll
-    for (int u = 1; u < U; ++u) {
+    for (int u = 1; u < P; ++u) {
         if ((uint32_t)u < NR) {
             wave_ld<V>(SY0 + ol, rc[u][0]);
             wave_ld<V>(SY1 + ol, rc[u][1]);
@@ -490,10 +500,10 @@ __global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) 
         T.L = L; T.W = W; T.plane = plane32; T.NR = NR; T.j = j;
         T.ol = ol; T.os = os; T.own = own;
         for (uint32_t R0 = 0; R0 < NR; R0 += U) {
-            if (R0 >= 4u * K + 2u && R0 + 2u * U <= NR)
-                wave_block01<K, V, U, DP, DQ, false>(a.R, T, h, rc, R0);
+            if (R0 >= 4u * K + 2u && R0 + U + P <= NR)
+                wave_block01<K, V, U, P, DP, DQ, false>(a.R, T, h, rc, R0);
             else
-                wave_block01<K, V, U, DP, DQ, true>(a.R, T, h, rc, R0);
+                wave_block01<K, V, U, P, DP, DQ, true>(a.R, T, h, rc, R0);
             wave_slide<K, V, U>(h);
         }
     } else {
@@ -503,10 +513,10 @@ __global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) 
             for (int u = 0; u < U; ++u) {
                 const uint32_t R = R0 + (uint32_t)u;
                 if (R >= NR) break;
-                if (R > 0) wave_convert_row<V>(h[base + u], h[base + u - 1], rc[u]);
-                if (R + U < NR) {               // row R + U into the ring entry just freed
-                    wave_ld<V>(SY0 + ol, rc[u][0]);
-                    wave_ld<V>(SY1 + ol, rc[u][1]);
+                if (R > 0) wave_convert_row<V>(h[base + u], h[base + u - 1], rc[u % P]);
+                if (R + P < NR) {               // row R + P into the ring entry just freed
+                    wave_ld<V>(SY0 + ol, rc[u % P][0]);
+                    wave_ld<V>(SY1 + ol, rc[u % P][1]);
                 }
                 ol += W;
                 if (ol >= plane32) ol -= plane32;
