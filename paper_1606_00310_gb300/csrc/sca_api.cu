@@ -257,8 +257,9 @@ int sca_set_temporal_block(sca_sim *s, int mcs_per_launch)
 // Automatic kernel choice (measured on GB300).  For a surface state the register-wavefront
 // kernel (4) wins wherever the lattice gives it enough tiles: with {0, 1} probabilities from
 // L = 4096 on (8 MCS per launch up to L = 8192, 16 above); with dyadic draws from L = 32768 on
-// for one or two draws per word (2 MCS per launch) and from L = 65536 on for three (1 MCS per
-// launch: the three Philox chains leave no registers for a deeper window); four or more draws
+// for one or two draws per word and from L = 65536 on for three (MCS per launch: 4 for one draw
+// with q = 0, 1 for three draws with q != 0 -- the Philox chains leave no registers for a deeper
+// window -- and 2 otherwise); four or more draws
 // run at the fused kernel's speed or below.  Otherwise the fused kernel halves HBM traffic once
 // the state is far larger than L2 and the update is not arithmetic-bound; shared-memory
 // temporal blocking (several MCS per launch) wins while the lattice is small enough that
@@ -268,7 +269,9 @@ static uint32_t wave_default_k(uint32_t L, const Rule &R)
 {
     if (R.mode == 0) return L >= 16384 ? 16u : 8u;
     if (R.mode == 2) return 2u;
-    return R.n_draws >= 3 ? 1u : 2u;
+    const bool q0 = R.nq == 0 && R.Pq == 0;
+    if (R.n_draws == 1 && q0) return 4u;       // p = 1/2: the lightest draws, the deepest window
+    return R.n_draws >= 3 && !q0 ? 1u : 2u;
 }
 
 static bool wave_auto(const sca_sim *s)

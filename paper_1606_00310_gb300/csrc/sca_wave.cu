@@ -51,7 +51,7 @@ static cudaError_t launch_mode0(const WaveArgs &a, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-int wave_max_k(int mode) { return mode == 0 ? 16 : mode == 1 ? 2 : mode == 2 ? 2 : 0; }
+int wave_max_k(int mode) { return mode == 0 ? 16 : mode == 1 ? 4 : mode == 2 ? 2 : 0; }
 
 uint32_t wave_pick_k(uint32_t want, int mode)
 {

@@ -50,6 +50,7 @@ static cudaError_t dispatch(const WaveArgs &a, int K, int V, int grid, cudaStrea
     switch (K) {
     case 1: return dispatch_k<1>(a, V, grid, st, blocks);
     case 2: return dispatch_k<2>(a, V, grid, st, blocks);
+    case 4: return dispatch_k<4>(a, V, grid, st, blocks);
     default: return cudaErrorInvalidValue;
     }
 }

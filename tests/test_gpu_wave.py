@@ -48,6 +48,9 @@ WAVE_CASES = [
     # p = 1 with dyadic q, and p = 0 (run-time draw loop)
     (2048, 0.875, 0.125, 2, 0), (1024, 0.625, 0.0, 2, 3), (512, 0.5, 0.5, 1, 0),
     (768, 0.75, 0.0, 2, 0), (1280, 1.0, 0.25, 2, 0), (1536, 0.0, 0.5, 2, 0),
+    # the same at 4 MCS per launch
+    (2048, 0.875, 0.125, 4, 0), (1024, 0.625, 0.0, 4, 3), (512, 0.5, 0.5, 4, 0), (768, 0.75, 0.0, 4, 0),
+    (1280, 1.0, 0.25, 4, 0), (2560, 0.5, 0.0, 4, 0),
 ]
 
 
