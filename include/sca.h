@@ -271,6 +271,13 @@ int sca_batch_unit_times(sca_batch *b, uint64_t *start_ns, uint64_t *end_ns,
 /* Canonical words of lattice `index` (4 * L * L/64 words) to host memory; synchronises. */
 int sca_batch_get_state(sca_batch *b, uint32_t index, uint32_t *host_words, size_t n_words);
 
+/* Canonical words of lattice `index` (4 * L * L/64 words, the layout of sca_set_state) from host
+ * memory; the batch time is unchanged, so the lattice continues from MCS sca_batch_time(b).  The
+ * state must be a surface (every plaquette closes, row 0 and column 0 close around the torus):
+ * both engines update height bits.  Synchronises.  Errors: SCA_EINVAL (bad index or short
+ * buffer), SCA_ESTATE (not a surface: the lattice is reset to flat), SCA_ECUDA. */
+int sca_batch_set_state(sca_batch *b, uint32_t index, const uint32_t *host_words, size_t n_words);
+
 /* All lattices back to flat at MCS 0 (asynchronous). */
 int sca_batch_reset(sca_batch *b);
 uint64_t sca_batch_time(const sca_batch *b);

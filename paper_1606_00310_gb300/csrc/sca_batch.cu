@@ -1530,6 +1530,35 @@ int sca_batch_get_state(sca_batch *b, uint32_t index, uint32_t *host_words, size
     return e == cudaSuccess ? SCA_OK : cuda_fail(e, "sca_batch_get_state");
 }
 
+int sca_batch_set_state(sca_batch *b, uint32_t index, const uint32_t *host_words, size_t n_words)
+{
+    if (!b || !host_words || index >= b->count) return fail(SCA_EINVAL, "bad argument");
+    const uint32_t L = b->lat[index].L;
+    const size_t need = (size_t)L * L / 16;
+    if (n_words < need) return fail(SCA_EINVAL, "host buffer too small");
+    uint32_t *dst = b->state + b->state_off[index];
+    uint32_t *scratch = nullptr;
+    bool surface = false;
+    cudaError_t e = cudaMemcpyAsync(dst, host_words, need * sizeof(uint32_t), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&scratch, 4 * sizeof(uint32_t), b->stream);
+    if (e == cudaSuccess) e = surface_check(dst, L, scratch, b->stream, &surface);
+    if (scratch) {
+        const cudaError_t e2 = cudaFreeAsync(scratch, b->stream);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sca_batch_set_state");
+    if (!surface) {
+        // both engines update height bits, exact for surfaces only: back to flat, refused
+        const size_t bytes = need * sizeof(uint32_t);
+        e = cudaMemsetAsync(dst, 0x00, bytes / 2, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync((char *)dst + bytes / 2, 0xFF, bytes / 2, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        return fail(SCA_ESTATE, "the state is not a surface (a plaquette or row 0 / column 0 does not close)");
+    }
+    return SCA_OK;
+}
+
 uint64_t sca_batch_time(const sca_batch *b) { return b ? b->t : 0; }
 
 int sca_batch_unit_times(sca_batch *b, uint64_t *start_ns, uint64_t *end_ns, int32_t *first_lattice,

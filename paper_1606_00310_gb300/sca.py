@@ -81,6 +81,7 @@ SIGNATURES = {
     "sca_batch_run": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.c_uint32, C.c_void_p,
                                 C.c_void_p]),
     "sca_batch_get_state": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t]),
+    "sca_batch_set_state": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t]),
     "sca_batch_unit_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32]),
     "sca_batch_reset": (C.c_int, [C.c_void_p]),
     "sca_batch_time": (C.c_uint64, [C.c_void_p]),
@@ -425,6 +426,12 @@ class Batch:
         check(load().sca_batch_get_state(self._h, int(index), out.ctypes.data_as(C.c_void_p), n),
               "sca_batch_get_state")
         return out
+
+    def set_state(self, index: int, words: np.ndarray):
+        """Lattice `index` from canonical words (a surface); the batch time is unchanged."""
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        check(load().sca_batch_set_state(self._h, int(index), w.ctypes.data_as(C.c_void_p), w.size),
+              "sca_batch_set_state")
 
     def reset(self):
         check(load().sca_batch_reset(self._h), "sca_batch_reset")

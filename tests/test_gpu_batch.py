@@ -202,3 +202,71 @@ def test_engine_choice(sca):
         assert b.engine() == 2
         with pytest.raises(sca.ScaError):
             b.set_engine(3)
+
+
+# {0, 1} rules from a flat surface are fixed points of every MCS, so the engines' {0, 1} paths
+# are checked from rough surfaces loaded with sca_batch_set_state (made by dyadic runs: the
+# oracle's for the small lattices, the two-pass kernel's for the large ones).
+ROUGH_MIX = [
+    dict(L=128, p=1.0, q=0.0, seed=41), dict(L=128, p=0.0, q=1.0, seed=42),
+    dict(L=256, p=1.0, q=1.0, seed=43), dict(L=512, p=1.0, q=0.0, seed=44),
+    dict(L=1024, p=1.0, q=0.0, seed=45), dict(L=2048, p=1.0, q=0.0, seed=46),
+    dict(L=256, p=0.75, q=0.25, seed=47), dict(L=2048, p=0.875, q=0.125, seed=48),
+]
+
+
+def _rough_words(sca, L, i):
+    if L <= 256:
+        bx, by = o.init_flat(L)
+        o.run(bx, by, 100 + i, 0.625, 0.375, t0=0, n_mcs=5)
+        return o.pack(bx, by)
+    with sca.Sim(L, seed=100 + i, p=0.625, q=0.375, kernel=sca.KERNEL_TWO_PASS) as sim:
+        sim.step(5)
+        return sim.get_state()
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_batch_from_rough_surfaces(sca, engine):
+    """Both engines, every {0, 1} rule and two dyadic ones, from rough surfaces: identical to a
+    single-lattice simulation (two-pass kernel) from the same surface, and to the oracle for
+    the small lattices."""
+    starts = [_rough_words(sca, d["L"], i) for i, d in enumerate(ROUGH_MIX)]
+    times = [3, 16, 37]
+    with sca.Batch(ROUGH_MIX) as b:
+        b.set_engine(engine)
+        for i, w in enumerate(starts):
+            b.set_state(i, w)
+        obs, _ = b.run(times)
+        words = [b.get_state(i) for i in range(len(ROUGH_MIX))]
+    for i, d in enumerate(ROUGH_MIX):
+        with sca.Sim(d["L"], seed=d["seed"], p=d["p"], q=d["q"], kernel=sca.KERNEL_TWO_PASS) as sim:
+            sim.set_state(starts[i], t=0)
+            ref = sim.run(times)
+            ref_words = sim.get_state()
+        assert [(g.S1, g.S2, g.num) for g in obs[i]] == [(g.S1, g.S2, g.num) for g in ref], d
+        assert np.array_equal(words[i], ref_words), d
+        if d["L"] <= 256:
+            bx, by = o.unpack(d["L"], starts[i])
+            t = 0
+            for tt, g in zip(times, obs[i]):
+                o.run(bx, by, d["seed"], d["p"], d["q"], t0=t, n_mcs=tt - t)
+                t = tt
+                r = o.observe(bx, by)
+                assert (g.S1, g.S2, g.num) == (r["S1"], r["S2"], r["num"]), d
+            assert np.array_equal(words[i], o.pack(bx, by)), d
+
+
+def test_batch_set_state_refuses_a_non_surface(sca):
+    with sca.Batch([dict(L=128, p=1.0, q=0.0, seed=1), dict(L=256, p=0.75, q=0.25, seed=2)]) as b:
+        bx, by = o.init_flat(128)
+        w = o.pack(bx, by)
+        w[5] ^= 1 << 7
+        with pytest.raises(sca.ScaError) as ei:
+            b.set_state(0, w)
+        assert ei.value.code == sca.ESTATE
+        flat = o.pack(*o.init_flat(128))
+        assert np.array_equal(b.get_state(0), flat)
+        import ctypes
+        assert sca.load().sca_batch_set_state(b._h, 2, flat.ctypes.data_as(ctypes.c_void_p), flat.size) == sca.EINVAL
+        short = flat[:10].copy()
+        assert sca.load().sca_batch_set_state(b._h, 0, short.ctypes.data_as(ctypes.c_void_p), short.size) == sca.EINVAL

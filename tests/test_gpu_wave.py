@@ -180,3 +180,72 @@ def test_wave_largest_lattice_p1_closed_form(sca):
         assert torch.equal(sim.state_tensor(), flat)
         del flat
     assert all(4 * g.num == g.N ** 2 and g.status == 0 for g in obs)
+
+
+# p, q in {0, 1} from a flat surface is a fixed point of every MCS (p = 1), so the cases below
+# start from rough surfaces made by a dyadic rule: the oracle's at small L, the two-pass
+# kernel's at large L.  16 MCS per launch is the default for L >= 16384 and is forced below it.
+def _rough_gpu(sca, L, mcs, seed=31):
+    with sca.Sim(L, seed=seed, p=0.625, q=0.375, kernel=sca.KERNEL_TWO_PASS) as sim:
+        sim.step(mcs)
+        return sim.get_state()
+
+
+def _run_from(sca, L, p, q, words, times, kernel, k=None, bands=None):
+    with sca.Sim(L, seed=5, p=p, q=q) as sim:
+        sim.set_state(words, t=0)
+        sim.set_kernel(kernel)
+        if k is not None:
+            sim.set_temporal_block(k)
+        if bands is not None:
+            sim.set_wave_bands(bands)
+        assert sim.kernel_in_use() == kernel
+        obs = sim.run(times)
+        return [(g.S1, g.S2, g.num) for g in obs], sim.get_state()
+
+
+@pytest.mark.parametrize("L,p,q,times,k", [(256, 1.0, 0.0, [48], 16), (320, 0.0, 1.0, [33, 80], 16),
+                                           (448, 1.0, 1.0, [16, 64, 65], 16), (1024, 1.0, 0.0, [7, 71, 200], 16),
+                                           (512, 1.0, 0.0, [9, 40], 8)])
+def test_wave01_rough_against_oracle(sca, L, p, q, times, k):
+    bx, by = o.init_flat(L)
+    o.run(bx, by, 31, 0.625, 0.375, t0=0, n_mcs=6)
+    got = _run_from(sca, L, p, q, o.pack(bx, by), times, sca.KERNEL_WAVE, k=k)
+    t = 0
+    for tt, g in zip(times, got[0]):
+        o.run(bx, by, 5, p, q, t0=t, n_mcs=tt - t)
+        t = tt
+        r = o.observe(bx, by)
+        assert g == (r["S1"], r["S2"], r["num"])
+    assert np.array_equal(got[1], o.pack(bx, by))
+
+
+@pytest.mark.parametrize("L,p,q,times,k,bands", [
+    (4096, 1.0, 0.0, [40, 200], 16, None), (8192, 0.0, 1.0, [64, 96], 16, None),
+    (6144, 1.0, 1.0, [35, 99], 16, None), (16384, 1.0, 0.0, [32, 160], None, None),
+    (4096, 1.0, 0.0, [80], 16, 31), (2048, 1.0, 0.0, [96], 16, 2), (1984, 1.0, 0.0, [64], 16, None),
+    (8192, 1.0, 0.0, [24, 88], 8, 5)])
+def test_wave01_rough_equals_two_pass(sca, L, p, q, times, k, bands):
+    words = _rough_gpu(sca, L, 5)
+    got = _run_from(sca, L, p, q, words, times, sca.KERNEL_WAVE, k=k, bands=bands)
+    ref = _run_from(sca, L, p, q, words, times, sca.KERNEL_TWO_PASS)
+    assert got[0] == ref[0]
+    assert np.array_equal(got[1], ref[1])
+
+
+@pytest.mark.parametrize("L,times", [(65536, [50, 178]), (131072, [3, 40])])
+def test_wave01_rough_full_size(sca, L, times):
+    """The benchmark's lattice and the largest one, from a rough surface: the automatic choice
+    (16 MCS per launch and the shorter launches up to each observation time) equals the two-pass
+    kernel, device states and exact sums."""
+    import torch
+    words = _rough_gpu(sca, L, 3 if L == 65536 else 2)
+    res = []
+    for kernel in (sca.KERNEL_WAVE, sca.KERNEL_TWO_PASS):
+        with sca.Sim(L, seed=5, p=1.0, q=0.0, kernel=kernel) as sim:
+            sim.set_state(words, t=0)
+            assert sim.kernel_in_use() == kernel
+            obs = sim.run(times)
+            res.append(([(g.S1, g.S2, g.num) for g in obs], sim.state_tensor().clone()))
+    assert res[0][0] == res[1][0]
+    assert torch.equal(res[0][1], res[1][1])
