@@ -603,6 +603,37 @@ def run_ours(a, rank, world, local_rank):
                  "hbm_frac_state_once_per_launch":
                      BYTES_PER_UPDATE * L * L * h_launches / (h_upd_ms / 1000.0) / 1e9 / peak}
 
+    # context: the same rule and kernel from a rough surface (a flat surface is a fixed point of
+    # p = 1; the kernel's work does not depend on the state, and this measures it)
+    rough = None
+    if not a.no_extra and rank == 0 and world == 1 and (a.p, a.q) == (1.0, 0.0):
+        prep = sca.Sim(L, seed=7, p=0.625, q=0.375, stream=stream, kernel=sca.KERNEL_TWO_PASS)
+        prep.step(3)
+        words = prep.get_state()
+        prep.close()
+        del prep
+        rs = sca.Sim(L, seed=1, p=1.0, q=0.0, stream=stream, kernel=a.kernel)
+        rs.set_state(words, t=0)
+        del words
+        rs.step(16)
+        torch.cuda.synchronize(dev)
+        n_rough = 256
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rs.step(n_rough)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        rms = e0.elapsed_time(e1)
+        w2 = rs.observe().w2
+        r_kern = rs.kernel_in_use()
+        rs.close()
+        del rs
+        rough = {"workload": "L=%d p=1 q=0 from a rough surface (3 MCS of p=5/8 q=3/8), %d MCS of "
+                             "updates only" % (L, n_rough),
+                 "value": L * L * n_rough / (rms / 1000.0), "unit": UNIT, "kernel": r_kern,
+                 "w2_after": w2}
+
     batched = None
     if not a.no_batch and rank == 0 and world == 1 and (a.L, a.p, a.q) == (65536, 1.0, 0.0):
         batched = run_batched(sca, torch, stream, dev, L, peak)
@@ -630,6 +661,8 @@ def run_ours(a, rank, world, local_rank):
                 "w2_final": obs[-1].w2}
         if extra:
             line["context_p_half"] = extra
+        if rough:
+            line["context_rough_p1"] = rough
         if batched:
             line["batched"] = batched
         if serving:
