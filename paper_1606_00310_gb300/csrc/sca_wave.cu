@@ -13,17 +13,25 @@ int wave_dyadic_blocks_per_sm(const Rule &R, int K, int V);
 cudaError_t launch_wave_uniform(const WaveArgs &a, int K, int grid, cudaStream_t st);
 int wave_uniform_blocks_per_sm(int K);
 
-// Words per lane: dyadic draws take four (one Philox call per draw for the four words) when
-// the row length allows, else one; {0, 1} probabilities one.
-static int wave_V(uint32_t L, int mode) { return mode == 1 && (L / 64) % 4 == 0 ? 4 : 1; }
+// Words per lane, when the row length allows four: dyadic draws take four (one Philox call per
+// draw for the four words); {0, 1} probabilities take four at 1 or 2 MCS per launch, where the
+// launch streams at memory speed: a tile then owns 120 words, whole 32-byte sectors starting on
+// a sector, so no sector is written by two tiles (with one word per lane the 30-word tiles
+// share edge sectors that L2 evicted half-written and refilled from DRAM: 0.9 GB read per launch
+// at L = 65536 against 0.54 GB), and its loads are 16 bytes a lane.  Else one.
+static int wave_V(uint32_t L, int mode, uint32_t k)
+{
+    if ((L / 64) % 4 != 0) return 1;
+    return mode == 1 || (mode == 0 && k <= 2) ? 4 : 1;
+}
 
-template <int K, bool DP, bool DQ>
+template <int K, int V, bool DP, bool DQ>
 static int blocks_per_sm()
 {
     static int n = 0;
     if (n == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wave01_kernel<K, DP, DQ>(), 32 * kWaveWarps, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, wave01_kernel<K, V, DP, DQ>(), 32 * kWaveWarps, 0) !=
                 cudaSuccess || b <= 0)
             b = 1;
         n = b;
@@ -31,23 +39,23 @@ static int blocks_per_sm()
     return n;
 }
 
-template <int K>
+template <int K, int V>
 static int blocks_mode0(bool dp, bool dq)
 {
-    if (dp && dq) return blocks_per_sm<K, true, true>();
-    if (dp) return blocks_per_sm<K, true, false>();
-    if (dq) return blocks_per_sm<K, false, true>();
-    return blocks_per_sm<K, false, false>();
+    if (dp && dq) return blocks_per_sm<K, V, true, true>();
+    if (dp) return blocks_per_sm<K, V, true, false>();
+    if (dq) return blocks_per_sm<K, V, false, true>();
+    return blocks_per_sm<K, V, false, false>();
 }
 
-template <int K>
+template <int K, int V>
 static cudaError_t launch_mode0(const WaveArgs &a, int grid, cudaStream_t st)
 {
     const bool dp = a.R.Pp != 0, dq = a.R.Pq != 0;
-    if (dp && dq) wave01_kernel<K, true, true>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
-    else if (dp) wave01_kernel<K, true, false>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
-    else if (dq) wave01_kernel<K, false, true>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
-    else wave01_kernel<K, false, false>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    if (dp && dq) wave01_kernel<K, V, true, true>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else if (dp) wave01_kernel<K, V, true, false>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else if (dq) wave01_kernel<K, V, false, true>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
+    else wave01_kernel<K, V, false, false>()<<<grid, 32 * kWaveWarps, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -67,11 +75,11 @@ static int blocks_for(int K, int V, const Rule &R)
     if (R.mode == 2) return wave_uniform_blocks_per_sm(K);
     const bool dp = R.Pp != 0, dq = R.Pq != 0;
     switch (K) {
-    case 1: return blocks_mode0<1>(dp, dq);
-    case 2: return blocks_mode0<2>(dp, dq);
-    case 4: return blocks_mode0<4>(dp, dq);
-    case 8: return blocks_mode0<8>(dp, dq);
-    default: return blocks_mode0<16>(dp, dq);
+    case 1: return V == 4 ? blocks_mode0<1, 4>(dp, dq) : blocks_mode0<1, 1>(dp, dq);
+    case 2: return V == 4 ? blocks_mode0<2, 4>(dp, dq) : blocks_mode0<2, 1>(dp, dq);
+    case 4: return blocks_mode0<4, 1>(dp, dq);
+    case 8: return blocks_mode0<8, 1>(dp, dq);
+    default: return blocks_mode0<16, 1>(dp, dq);
     }
 }
 
@@ -82,7 +90,7 @@ static bool wave_plan(uint32_t L, uint32_t k, int mode, uint32_t bands, int bloc
 {
     if (L < 64 || L % 64 != 0 || k == 0 || (k & (k - 1)) != 0) return false;
     if ((int)k > wave_max_k(mode)) return false;
-    const uint32_t W = L / 64, tw = kWaveTileWords * (uint32_t)wave_V(L, mode);
+    const uint32_t W = L / 64, tw = kWaveTileWords * (uint32_t)wave_V(L, mode, k);
     const uint32_t nc = (W + tw - 1) / tw;
     uint32_t nb = bands;
     if (nb == 0) {
@@ -110,7 +118,7 @@ cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t
     const int mode = (int)R.mode;
     uint32_t nb, nc;
     if (!wave_plan(L, k, mode, bands, 1, &nb, &nc)) return cudaErrorInvalidValue;
-    const int V = wave_V(L, mode);
+    const int V = wave_V(L, mode, k);
     if (!wave_plan(L, k, mode, bands, blocks_for((int)k, V, R), &nb, &nc)) return cudaErrorInvalidValue;
     const WaveArgs a{src, dst, L, L / 64, nb, nc, t0, t_dev, R};
     const uint64_t tiles = (uint64_t)nb * nc;
@@ -119,11 +127,11 @@ cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t
     if (mode == 1) return launch_wave_dyadic(a, (int)k, V, grid, st);
     if (mode == 2) return launch_wave_uniform(a, (int)k, grid, st);
     switch (k) {
-    case 1: return launch_mode0<1>(a, grid, st);
-    case 2: return launch_mode0<2>(a, grid, st);
-    case 4: return launch_mode0<4>(a, grid, st);
-    case 8: return launch_mode0<8>(a, grid, st);
-    case 16: return launch_mode0<16>(a, grid, st);
+    case 1: return V == 4 ? launch_mode0<1, 4>(a, grid, st) : launch_mode0<1, 1>(a, grid, st);
+    case 2: return V == 4 ? launch_mode0<2, 4>(a, grid, st) : launch_mode0<2, 1>(a, grid, st);
+    case 4: return launch_mode0<4, 1>(a, grid, st);
+    case 8: return launch_mode0<8, 1>(a, grid, st);
+    case 16: return launch_mode0<16, 1>(a, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }

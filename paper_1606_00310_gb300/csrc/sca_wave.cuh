@@ -533,11 +533,11 @@ __global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) 
     }
 }
 
-// The kernel that runs K MCS per launch with {0, 1} probabilities.
-template <int K, bool DP, bool DQ>
+// The kernel that runs K MCS per launch with {0, 1} probabilities, V words per lane.
+template <int K, int V, bool DP, bool DQ>
 constexpr void (*wave01_kernel())(WaveArgs)
 {
-    return k_wave<K, 1, kWaveU0, 0, DP, DQ>;
+    return k_wave<K, V, kWaveU0, 0, DP, DQ>;
 }
 
 }  // namespace sca
