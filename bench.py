@@ -634,6 +634,29 @@ def run_ours(a, rank, world, local_rank):
                  "value": L * L * n_rough / (rms / 1000.0), "unit": UNIT, "kernel": r_kern,
                  "w2_after": w2}
 
+    # context: the wide system L = 2^17 (4 GiB of packed slopes per buffer), the paper's case
+    # p = 1/2 and the headline rule, updates only; the paper reports its wide system within 5 %
+    # of L = 2^16
+    wide = None
+    if not a.no_extra and rank == 0 and world == 1 and (a.L, a.p, a.q) == (65536, 1.0, 0.0):
+        wide = {"workload": "L=131072 flat start, updates only (CUDA events)", "unit": UNIT}
+        for key, (wp, wq, n_w) in (("p_half", (0.5, 0.0, 32)), ("p1", (1.0, 0.0, 128))):
+            ws = sca.Sim(131072, seed=1, p=wp, q=wq, stream=stream, kernel=a.kernel)
+            ws.step(16)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ws.step(n_w)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            wide[key] = 131072.0 * 131072.0 * n_w / (e0.elapsed_time(e1) / 1000.0)
+            wide[key + "_kernel"] = ws.kernel_in_use()
+            ws.close()
+            del ws
+        if extra:
+            wide["p_half_ratio_to_L65536"] = wide["p_half"] / extra["value"]
+
     batched = None
     if not a.no_batch and rank == 0 and world == 1 and (a.L, a.p, a.q) == (65536, 1.0, 0.0):
         batched = run_batched(sca, torch, stream, dev, L, peak)
@@ -663,6 +686,8 @@ def run_ours(a, rank, world, local_rank):
             line["context_p_half"] = extra
         if rough:
             line["context_rough_p1"] = rough
+        if wide:
+            line["context_wide_L131072"] = wide
         if batched:
             line["batched"] = batched
         if serving:

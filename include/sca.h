@@ -171,17 +171,20 @@ uint64_t sca_time(const sca_sim *sim);
  * multiple of 2048), 3 = temporal blocking (several MCS per launch in shared memory, see
  * sca_set_temporal_block), 4 = register-wavefront temporal blocking (each warp streams a band
  * of rows through registers as one height bit per site and advances it up to 16 MCS per launch
- * with {0, 1} probabilities, 2 with dyadic draws or per-site uniforms; sca_step returns
+ * with {0, 1} probabilities, 4 with dyadic draws, 2 with per-site uniforms; sca_step returns
  * SCA_ESTATE if the state is not a surface, see sca_set_state).
  * Results are identical for every choice; only speed differs.
  * Errors: SCA_EINVAL (unknown kernel, or one that does not support this lattice or rule). */
 int sca_set_kernel(sca_sim *sim, int kernel);
 
 /* Temporal blocking (kernels 3 and 4 of sca_set_kernel): each launch advances mcs_per_launch
- * MCS (a divisor of 64; 0 = default: 4 for kernel 3, the most kernel 4 supports for the rule)
- * with a halo of 2 rows per MCS above and below every block of rows; kernel 4 caps a launch at
- * 16 MCS ({0, 1} probabilities) or 2 (random draws).  Errors: SCA_EINVAL if mcs_per_launch
- * does not divide 64 or, for kernel 3, the block with its halo does not fit for this L. */
+ * MCS (a divisor of 64) with a halo of 2 rows per MCS above and below every block of rows; 0 =
+ * default: 4 for kernel 3; for kernel 4 the measured best for the rule (with {0, 1}
+ * probabilities 16 from L = 16384 on and 8 below; with dyadic draws 4 for one draw and q = 0,
+ * 1 for three draws and q != 0, 2 otherwise; 2 with per-site uniforms).  Kernel 4 caps a launch
+ * at 16 MCS ({0, 1} probabilities), 4 (dyadic draws) or 2 (per-site uniforms).  Errors:
+ * SCA_EINVAL if mcs_per_launch does not divide 64 or, for kernel 3, the block with its halo does
+ * not fit for this L. */
 int sca_set_temporal_block(sca_sim *sim, int mcs_per_launch);
 
 /* Row bands of the register-wavefront kernel (kernel 4): the lattice is cut into `bands` bands
