@@ -22,11 +22,12 @@
 // together, all half-steps of one position agree on which side the shifted x-neighbour word
 // comes from (a compile-time fact after unrolling).
 //
-// Tiles.  Lane l of a warp owns one packed word of every row of its band; lanes 0 and 31 hold
-// halo words (the x light cone grows by at most one bit per half-step, so one word on each side
-// covers K <= 16) and bands carry 2K + 2 halo rows above and 2K below.  Halos are recomputed by the
-// neighbouring tiles from the same counter-based random bits, so tiles never communicate;
-// they read the source buffer and write only their own words of the destination buffer.
+// Tiles.  Lane l of a warp owns V consecutive packed words of every row of its band (V = 1, or
+// 4 where one Philox call serves four words or the launch streams at memory speed); lanes 0 and
+// 31 hold halo words (the x light cone grows by at most one bit per half-step, so one word on
+// each side covers K <= 16) and bands carry 2K + 2 halo rows above and 2K below.  Halos are
+// recomputed by the neighbouring tiles from the same counter-based random bits, so tiles never
+// communicate; they read the source buffer and write only their own words of the destination.
 #pragma once
 #include "sca_internal.h"
 
