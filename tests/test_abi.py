@@ -72,3 +72,17 @@ def test_init_rejects_bad_parameters_on_host(lib, L, p, q, rng):
 def test_strerror_names_every_status(lib):
     for code in range(0, -10, -1):
         assert lib.sca_strerror(code) not in (None, b"unknown status")
+
+
+def test_null_handles_are_refused_on_host(lib):
+    """Every entry point that takes a simulation, batch or server handle refuses NULL with
+    SCA_EINVAL before touching a device."""
+    import paper_1606_00310_gb300.sca as sca
+    buf = (C.c_uint32 * 16)()
+    assert lib.sca_batch_set_state(None, 0, buf, 16) == sca.EINVAL
+    assert lib.sca_batch_get_state(None, 0, buf, 16) == sca.EINVAL
+    assert lib.sca_batch_reset(None) == sca.EINVAL
+    assert lib.sca_set_wave_bands(None, 0) == sca.EINVAL
+    assert lib.sca_set_temporal_block(None, 0) == sca.EINVAL
+    assert lib.sca_set_kernel(None, 0) == sca.EINVAL
+    assert lib.sca_step(None, 1) == sca.EINVAL
