@@ -224,7 +224,9 @@ def test_wave01_rough_against_oracle(sca, L, p, q, times, k):
     (4096, 1.0, 0.0, [40, 200], 16, None), (8192, 0.0, 1.0, [64, 96], 16, None),
     (6144, 1.0, 1.0, [35, 99], 16, None), (16384, 1.0, 0.0, [32, 160], None, None),
     (4096, 1.0, 0.0, [80], 16, 31), (2048, 1.0, 0.0, [96], 16, 2), (1984, 1.0, 0.0, [64], 16, None),
-    (8192, 1.0, 0.0, [24, 88], 8, 5)])
+    (8192, 1.0, 0.0, [24, 88], 8, 5),
+    # four words per lane (1 and 2 MCS per launch): several tiles, uneven bands
+    (8192, 1.0, 0.0, [10, 31], 2, None), (4096, 0.0, 1.0, [9], 1, 7), (6144, 1.0, 1.0, [5, 12], 2, 3)])
 def test_wave01_rough_equals_two_pass(sca, L, p, q, times, k, bands):
     words = _rough_gpu(sca, L, 5)
     got = _run_from(sca, L, p, q, words, times, sca.KERNEL_WAVE, k=k, bands=bands)
