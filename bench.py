@@ -215,6 +215,30 @@ def aggregate_replicas(local_updates, local_seconds, dist=None, device=None):
 
 
 # ----------------------------------------------------------------------------- oracle arm
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), with the architecture."""
+    import platform
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        name = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return "%s (%s)" % (name or "unknown", platform.machine())
+
+
 def oracle_sample(L, p, q, seconds, seed=1, threads=0):
     """Time the CPU oracle on a band of rows of the same lattice (full width L), enough MCS
     for about `seconds` of work, on all host cores (or `threads`).  Returns (updates_per_s,
@@ -262,7 +286,7 @@ def run_reference(a, rank, world):
             "data": "synthetic (flat initial surface, seeded Philox)", "impl": "reference",
             "config": config(a, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": descs[-1]},
+                             "sample": descs[-1], "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -468,9 +492,10 @@ def run_ours(a, rank, world, local_rank):
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         apeak, mhz = alu_peak_tops(n_sm)
         achieved = WAVE_ALU_OPS_PER_UPDATE * upd_total / upd_s / 1e12
-        state_bytes = 0.5 * L * L           # canonical words: two slope bits per site
+        state_bytes = L * L / 4.0           # canonical words: two slope bits per site
+        traffic = recorded_traffic("k_wave", L)
         roof = {"bound": "alu", "achieved": achieved, "peak": apeak, "unit": "Tops/s",
-                "frac": achieved / apeak, "traffic": recorded_traffic("k_wave", L),
+                "frac": achieved / apeak, "traffic": traffic,
                 "kernel": "k_wave",
                 "peak_source": "derived: %d SMs x %d logic lanes/clk x %.0f MHz (max SM clock)"
                                % (n_sm, ALU_LANES_PER_SM, mhz),
@@ -483,7 +508,10 @@ def run_ours(a, rank, world, local_rank):
                 "x_one_pass_hbm_roofline": (upd_total / upd_s) / (peak * 1e9 / BYTES_PER_UPDATE),
                 "avg_launch_ms": avg_launch_s * 1e3, "launches": upd_launches,
                 "mcs_per_launch_avg": a.mcs * a.steps / max(1, upd_launches),
+                # the canonical state (L^2/4 bytes) read and written once per launch
                 "hbm_GBs_state_once_per_launch": 2 * state_bytes * upd_launches / upd_s / 1e9,
+                # DRAM bytes per launch from the ncu capture over the live average launch time
+                "dram_GBs_measured": traffic / avg_launch_s / 1e9 if traffic else None,
                 "hbm_peak_GBs": peak,
                 "update_share_of_step": upd_ms / ms if ms > 0 else None,
                 "updates_per_s_kernel_only": upd_total / upd_s}
@@ -672,7 +700,7 @@ def run_ours(a, rank, world, local_rank):
         r, cores, desc = oracle_sample(L, a.p, a.q, a.cpu_seconds)
         r1, _, desc1 = oracle_sample(L, a.p, a.q, max(1.0, a.cpu_seconds / 3), threads=1)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
-               "value_1_core": r1, "sample_1_core": desc1}
+               "cpu_model": cpu_model(), "value_1_core": r1, "sample_1_core": desc1}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

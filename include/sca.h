@@ -328,6 +328,17 @@ int sca_server_create(size_t budget_bytes, uint32_t max_active, uint32_t max_L, 
 int sca_server_submit(sca_server *srv, const sca_params *params, uint64_t n_mcs,
                       const uint64_t *times, uint32_t n_times, uint64_t *ticket);
 
+/* As sca_server_submit, and the request's final state comes back too: when it finishes, its
+ * canonical words (4 * L * L/64 of them, the layout of sca_get_state) are copied into
+ * final_words, caller-owned host memory of n_words >= 4 * L * L/64 words that must stay valid
+ * until the request has finished (pinned memory keeps the copy asynchronous; pageable memory
+ * makes the scheduler thread wait for it).  The words are the result once the request's status
+ * is SCA_OK; after a cancellation or an error they are unspecified.  Errors: as
+ * sca_server_submit, and SCA_EINVAL for a NULL or short buffer. */
+int sca_server_submit_state(sca_server *srv, const sca_params *params, uint64_t n_mcs,
+                            const uint64_t *times, uint32_t n_times, uint32_t *final_words,
+                            size_t n_words, uint64_t *ticket);
+
 /* Result of a request without blocking: SCA_EBUSY while pending or running; otherwise its
  * final status, with up to n_out observations copied to out (may be NULL) and info filled (may
  * be NULL).  Errors: SCA_ENOTFOUND. */
@@ -357,10 +368,12 @@ void sca_server_destroy(sca_server *srv);
  * pool, a plug-in barred from the CUDA allocator, a loop that must not pay for cudaMalloc or
  * its implicit device synchronisation).  It computes the same exact roughness as sca_observe
  * for canonical words the caller already holds, using a fixed file-scope device array of
- * 590,336 bytes as scratch (held by every GPU that loads this library until the process exits).
+ * 66,048 bytes as scratch (held by every GPU that loads this library until the process exits):
+ * room for the row kernel's chunk records (at most 1024 chunks of at most 256 rows) and the
+ * result record.
  *   words_dev: caller-owned device memory with 4 * L * L/64 canonical words (read only).
- *   L:         multiple of 64, 64 <= L <= 65536; larger L is rejected with SCA_EINVAL because
- *              the column-0 heights would not fit the scratch array.
+ *   L:         multiple of 64, 64 <= L <= 131072 (the library's largest lattice); larger L is
+ *              rejected with SCA_EINVAL before any device work.
  *   t:         copied into out->t.
  *   stream:    cudaStream_t as void*, NULL for the legacy default stream; synchronised.
  *   out:       host result, as from sca_observe (SCA_ESTATE if the slopes do not close).
@@ -386,6 +399,15 @@ int sca_selftest_wait_timeout(uint32_t limit_us);
  * fills every SM, timed with CUDA events on a private stream (about 20 ms).  The denominator of
  * the height-bit update's ALU roofline.  Errors: SCA_EINVAL, SCA_ECUDA. */
 int sca_measure_logic_rate(double *ops_per_s);
+
+/* Measured rates of the multiply pipe on the current GPU, over the whole device, each from one
+ * launch that fills every SM, timed with CUDA events on a private stream (about 30 ms):
+ * wide_mul_per_s, 32 x 32 -> 64-bit multiply-adds per second (eight independent chains per
+ * thread); philox_calls_per_s, Philox4x32-10 calls per second as the update kernels compute
+ * them (ten rounds of two such products each, four independent counters per thread).  The
+ * denominators of the rooflines of the paths that draw random numbers (Sec. II.B, Sec. III).
+ * Errors: SCA_EINVAL, SCA_ECUDA. */
+int sca_measure_mul_rate(double *wide_mul_per_s, double *philox_calls_per_s);
 
 /* Number of kernels this library has launched in this process (all objects, all streams). */
 uint64_t sca_kernel_launches(void);

@@ -51,6 +51,8 @@ int make_rule(const sca_params &prm, Rule &R)
     std::memset(&R, 0, sizeof(R));
     R.k0 = (uint32_t)prm.seed;
     R.k1 = (uint32_t)(prm.seed >> 32);
+    R.one = 1u;
+    R.two = 2u;
     for (uint32_t r = 0; r < 10; ++r) {          // Philox key schedule, round r
         R.rk[2 * r] = R.k0 + r * 0x9E3779B9u;
         R.rk[2 * r + 1] = R.k1 + r * 0xBB67AE85u;

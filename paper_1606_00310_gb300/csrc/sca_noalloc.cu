@@ -5,8 +5,8 @@
 // call the CUDA allocator, or a latency-sensitive loop that must not pay for (or fail in)
 // cudaMalloc, which can also synchronise the device.  Such callers already hold the lattice's
 // canonical words in memory they allocated themselves.  For them this entry point runs the
-// same three observation kernels as sca_observe, with their scratch (column-0 heights, block
-// partial sums, the result record) in one file-scope device array instead of an allocation.
+// same observation kernels as sca_observe, with their scratch (the per-chunk records of the row
+// kernel and the result record) in one file-scope device array instead of an allocation.
 //
 // The array is static: every GPU that loads this library holds kScratchBytes of it until the
 // process exits.  All calls on a device share it, so calls that overlap on the GPU (two
@@ -24,14 +24,15 @@ namespace sca {
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *where);
 
-constexpr uint32_t kNoAllocMaxL = 65536;
-// layout: column-0 heights (int64 per row), block partials (+1 for the column flag), result
-constexpr size_t kH0Bytes = (size_t)kNoAllocMaxL * sizeof(int64_t);
-constexpr size_t kPartOff = kH0Bytes;
+// The library's largest lattice.  The row kernel reduces at most kObsChunkCap chunks of at most
+// 256 rows each (obs_partials), which covers it; the chunk records take two partial slots each.
+constexpr uint32_t kNoAllocMaxL = 131072;
+// layout: the partial slots (kObsGridCap + 1 of them, the chunk records), then the result record
 constexpr size_t kPartBytes = ((size_t)(kObsGridCap + 1) * sizeof(ObsPartial) + 255) & ~(size_t)255;
-constexpr size_t kResOff = kPartOff + kPartBytes;
+constexpr size_t kResOff = kPartBytes;
 constexpr size_t kScratchBytes = kResOff + 256;
 static_assert(sizeof(ObsDev) <= 256, "result record fits");
+static_assert(kScratchBytes == 66048, "the size the header states");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -69,16 +70,17 @@ extern "C" int sca_observe_noalloc(const uint32_t *words_dev, uint32_t L, uint64
     if (L < 64 || L % 64 != 0)
         return fail(SCA_EINVAL, "L must be a positive multiple of 64");
     if (L > kNoAllocMaxL)
-        return fail(SCA_EINVAL, "L exceeds the no-allocation scratch limit of 65536");
+        return fail(SCA_EINVAL, "L exceeds the library's largest lattice, 131072");
+    if (obs_partials(L) > kObsGridCap / 2)
+        return fail(SCA_EINVAL, "L needs more chunk records than the scratch array holds");
     void *base = nullptr;
     cudaError_t e = scratch_for_current_device(&base);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
     unsigned char *b = static_cast<unsigned char *>(base);
-    int64_t *h0 = reinterpret_cast<int64_t *>(b);
-    ObsPartial *part = reinterpret_cast<ObsPartial *>(b + kPartOff);
+    ObsPartial *part = reinterpret_cast<ObsPartial *>(b);
     ObsDev *res = reinterpret_cast<ObsDev *>(b + kResOff);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    e = launch_observe(words_dev, L, h0, part, res, t, st);
+    e = launch_observe(words_dev, L, nullptr, part, res, t, st);
     if (e != cudaSuccess) return cuda_fail(e, "observe launch");
     e = cudaMemcpyAsync(out, res, sizeof(ObsDev), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -48,6 +48,7 @@ struct ServeReq {
     size_t need = 0;
     int slot = -1;
     std::vector<sca_obs> obs;
+    uint32_t *final_words = nullptr;    // caller-owned host buffer for the final state (or null)
     // scheduler-owned while active
     void *mem = nullptr;
     sca_sim *sim = nullptr;
@@ -227,6 +228,11 @@ static int enqueue_piece(sca_server *srv, ServeReq *r)
     if (r->next_obs == n) {
         cudaError_t e = cudaMemcpyAsync(sl.pinned, s->res, n * sizeof(sca_obs), cudaMemcpyDeviceToHost, sl.stream);
         if (e != cudaSuccess) return cuda_fail(e, "result copy");
+        if (r->final_words) {
+            e = cudaMemcpyAsync(r->final_words, s->buf[s->cur], s->lo.state_bytes, cudaMemcpyDeviceToHost,
+                                sl.stream);
+            if (e != cudaSuccess) return cuda_fail(e, "final state copy");
+        }
         r->copying = true;
     } else {
         const uint64_t gap = r->times[r->next_obs] - s->t;
@@ -385,10 +391,12 @@ int sca_server_create(size_t budget_bytes, uint32_t max_active, uint32_t max_L, 
     return SCA_OK;
 }
 
-int sca_server_submit(sca_server *srv, const sca_params *params, uint64_t n_mcs,
-                      const uint64_t *times, uint32_t n_times, uint64_t *ticket)
+static int submit_impl(sca_server *srv, const sca_params *params, uint64_t n_mcs, const uint64_t *times,
+                       uint32_t n_times, uint32_t *final_words, size_t n_words, uint64_t *ticket)
 {
     if (!srv || !params || !ticket || n_mcs == 0) return fail(SCA_EINVAL, "NULL argument or zero MCS");
+    if (final_words && n_words < 4 * (size_t)params->L * (params->L / 64))
+        return fail(SCA_EINVAL, "final-state buffer shorter than 4 * L * L/64 words");
     if (params->L > srv->max_L) return fail(SCA_EINVAL, "L exceeds the server's maximum");
     const size_t need = sca_workspace_bytes(params->L);
     if (need == 0) return fail(SCA_EINVAL, "L must be a multiple of 64 in [64, 131072]");
@@ -399,6 +407,7 @@ int sca_server_submit(sca_server *srv, const sca_params *params, uint64_t n_mcs,
     ServeReq *r = new ServeReq();
     r->P = *params;
     r->n_mcs = n_mcs;
+    r->final_words = final_words;
     if (times && n_times) {
         if (n_times > (uint32_t)kResCap) { delete r; return fail(SCA_EINVAL, "at most 64 observation times"); }
         uint64_t prev = 0;
@@ -431,6 +440,20 @@ int sca_server_submit(sca_server *srv, const sca_params *params, uint64_t n_mcs,
     }
     srv->cv_work.notify_one();
     return SCA_OK;
+}
+
+int sca_server_submit(sca_server *srv, const sca_params *params, uint64_t n_mcs,
+                      const uint64_t *times, uint32_t n_times, uint64_t *ticket)
+{
+    return submit_impl(srv, params, n_mcs, times, n_times, nullptr, 0, ticket);
+}
+
+int sca_server_submit_state(sca_server *srv, const sca_params *params, uint64_t n_mcs,
+                            const uint64_t *times, uint32_t n_times, uint32_t *final_words,
+                            size_t n_words, uint64_t *ticket)
+{
+    if (!final_words) return fail(SCA_EINVAL, "NULL final-state buffer");
+    return submit_impl(srv, params, n_mcs, times, n_times, final_words, n_words, ticket);
 }
 
 static int collect(sca_server *srv, ServeReq *r, sca_obs *out, uint32_t n_out, sca_request_info *info)

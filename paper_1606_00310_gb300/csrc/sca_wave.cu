@@ -230,7 +230,98 @@ __global__ void __launch_bounds__(256) k_logic_rate(uint32_t iters, uint32_t see
     if (x == 0x9E3779B9u) *sink = x;      // keeps the chains live; practically never taken
 }
 
+// Issue rate of 32 x 32 -> 64-bit multiplies (the product a Philox round takes twice): eight
+// independent chains per thread, each step d = lo(d) * M + d in one wide multiply-add.
+__global__ void __launch_bounds__(256) k_mul_rate(uint32_t iters, uint32_t seed, uint32_t *sink)
+{
+    uint64_t d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) d[k] = (uint64_t)(seed * (threadIdx.x + 1u) + (uint32_t)k) << 7;
+    const uint32_t M = 0xD2511F53u ^ (seed & 0xF0u);
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(d[k]) : "r"((uint32_t)d[k]), "r"(M));
+    }
+    uint64_t x = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x ^= d[k];
+    if ((uint32_t)x == 0x9E3779B9u) *sink = (uint32_t)(x >> 32);
+}
+
+// Philox4x32-10 calls per second as the update kernels compute them (philox4x32_10_rk with the
+// round keys in kernel parameters): four independent counters per thread and iteration.
+struct PhiloxKeys { uint32_t rk[20]; };
+__global__ void __launch_bounds__(256) k_philox_rate(uint32_t iters, PhiloxKeys K, uint32_t *sink)
+{
+    uint32_t acc = 0;
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const Ctr4 o = philox4x32_10_rk(Ctr4{g, i, (uint32_t)c, 0u}, K.rk);
+            acc ^= o.x ^ o.y ^ o.z ^ o.w;
+        }
+    }
+    if (acc == 0x9E3779B9u) *sink = acc;
+}
+
 }  // namespace sca
+
+// Multiply-pipe and Philox rates (see sca.h).
+extern "C" int sca_measure_mul_rate(double *wide_mul_per_s, double *philox_calls_per_s)
+{
+    using namespace sca;
+    if (!wide_mul_per_s || !philox_calls_per_s) return fail(SCA_EINVAL, "NULL argument");
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    uint32_t *sink = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventCreate(&e2);
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(uint32_t));
+    PhiloxKeys K;
+    for (int r = 0; r < 10; ++r) {
+        K.rk[2 * r] = 0x1234567u + (uint32_t)r * 0x9E3779B9u;
+        K.rk[2 * r + 1] = 0x89ABCDEu + (uint32_t)r * 0xBB67AE85u;
+    }
+    const uint32_t blocks = (uint32_t)sm_count() * 8u, threads = 256u, iters_m = 8000u, iters_p = 8000u;
+    float ms_m = 0.f, ms_p = 0.f;
+    if (e == cudaSuccess) {
+        k_mul_rate<<<blocks, threads, 0, st>>>(100u, 0x1234567u, sink);       // warm-up
+        k_philox_rate<<<blocks, threads, 0, st>>>(20u, K, sink);
+        count_launches(2);
+        e = cudaEventRecord(e0, st);
+    }
+    if (e == cudaSuccess) {
+        k_mul_rate<<<blocks, threads, 0, st>>>(iters_m, 0x7654321u, sink);
+        k_philox_rate<<<blocks, threads, 0, st>>>(1u, K, sink);               // keeps e1 after e0's work
+        count_launches(2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) {
+        k_philox_rate<<<blocks, threads, 0, st>>>(iters_p, K, sink);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e2, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e2);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_m, e0, e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_p, e1, e2);
+    if (sink) cudaFree(sink);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e2) cudaEventDestroy(e2);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return cuda_fail(e, "multiply-rate probe");
+    *wide_mul_per_s = (double)blocks * threads * iters_m * 128.0 / (ms_m * 1e-3);
+    *philox_calls_per_s = (double)blocks * threads * iters_p * 4.0 / (ms_p * 1e-3);
+    return SCA_OK;
+}
 
 extern "C" int sca_measure_logic_rate(double *ops_per_s)
 {

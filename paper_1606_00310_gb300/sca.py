@@ -63,6 +63,7 @@ SIGNATURES = {
     "sca_set_temporal_block": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_set_wave_bands": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_measure_logic_rate": (C.c_int, [C.POINTER(C.c_double)]),
+    "sca_measure_mul_rate": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "sca_batch_set_engine": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_batch_get_engine": (C.c_int, [C.c_void_p]),
     "sca_set_state_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint64]),
@@ -89,6 +90,8 @@ SIGNATURES = {
     "sca_server_create": (C.c_int, [C.c_size_t, C.c_uint32, C.c_uint32, C.POINTER(C.c_void_p)]),
     "sca_server_submit": (C.c_int, [C.c_void_p, C.POINTER(sca_params), C.c_uint64, C.c_void_p,
                                     C.c_uint32, C.POINTER(C.c_uint64)]),
+    "sca_server_submit_state": (C.c_int, [C.c_void_p, C.POINTER(sca_params), C.c_uint64, C.c_void_p,
+                                          C.c_uint32, C.c_void_p, C.c_size_t, C.POINTER(C.c_uint64)]),
     "sca_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32, C.c_void_p]),
     "sca_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_uint32,
                                   C.c_void_p]),
@@ -146,6 +149,14 @@ def measure_logic_rate() -> float:
     r = C.c_double()
     check(load().sca_measure_logic_rate(C.byref(r)), "sca_measure_logic_rate")
     return float(r.value)
+
+
+def measure_mul_rate():
+    """(32x32->64 multiply-adds per second, Philox4x32-10 calls per second) on this GPU."""
+    m = C.c_double()
+    p = C.c_double()
+    check(load().sca_measure_mul_rate(C.byref(m), C.byref(p)), "sca_measure_mul_rate")
+    return float(m.value), float(p.value)
 
 
 def kernel_launches() -> int:
@@ -467,17 +478,26 @@ class Server:
         check(lib.sca_server_create(int(budget_bytes), int(max_active), int(max_L), C.byref(h)),
               "sca_server_create")
         self._h = h
+        self._keep = {}         # final-state buffers of requests not yet released
 
-    def submit(self, L, p, q, seed, n_mcs, times=None, rng=RNG_AUTO) -> int:
+    def submit(self, L, p, q, seed, n_mcs, times=None, rng=RNG_AUTO, final_words=None) -> int:
+        """Queue a request; with final_words (a C-contiguous uint32 array of 4 * L * L/64 words,
+        kept alive here until the request is released) its final state comes back there."""
         prm = sca_params(L=int(L), rng=int(rng), seed=int(seed), p=float(p), q=float(q))
         tk = C.c_uint64()
-        if times:
-            arr = (C.c_uint64 * len(times))(*[int(x) for x in times])
-            rc = load().sca_server_submit(self._h, C.byref(prm), int(n_mcs), C.cast(arr, C.c_void_p),
-                                          len(times), C.byref(tk))
+        arr = (C.c_uint64 * len(times))(*[int(x) for x in times]) if times else None
+        tptr = C.cast(arr, C.c_void_p) if times else None
+        nt = len(times) if times else 0
+        if final_words is not None:
+            if final_words.dtype != np.uint32 or not final_words.flags["C_CONTIGUOUS"]:
+                raise ValueError("final_words must be a C-contiguous uint32 array")
+            rc = load().sca_server_submit_state(self._h, C.byref(prm), int(n_mcs), tptr, nt,
+                                                final_words.ctypes.data, final_words.size, C.byref(tk))
         else:
-            rc = load().sca_server_submit(self._h, C.byref(prm), int(n_mcs), None, 0, C.byref(tk))
+            rc = load().sca_server_submit(self._h, C.byref(prm), int(n_mcs), tptr, nt, C.byref(tk))
         check(rc, "sca_server_submit")
+        if final_words is not None:
+            self._keep[int(tk.value)] = final_words
         return int(tk.value)
 
     def _result(self, fn, ticket, *extra):
@@ -501,6 +521,7 @@ class Server:
 
     def release(self, ticket):
         check(load().sca_server_release(self._h, int(ticket)), "sca_server_release")
+        self._keep.pop(int(ticket), None)
 
     def stats(self) -> dict:
         st = sca_server_stats()

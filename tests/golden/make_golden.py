@@ -6,7 +6,13 @@ name the paper passage that justifies it) and expected values for small GPU pari
 Each case: lattice size L, seed, (p, q), mode (1 = dyadic, 2 = per-site uniform), observation
 times; stored: exact S1, S2, num at each time and the sha256 of the final canonical words.
 
-Run:  python tests/golden/make_golden.py
+The mid-size workload (L = 4096, 10^4 MCS, 40 log-spaced observation times, p = 3/4, q = 1/4,
+seeds 1-4) takes the oracle about 25 minutes per seed on 8 host cores; it is written to its own
+file, oracle_mid_size.json, one case at a time, so the GPU tests compare the full runs without
+running the oracle at test time.
+
+Run:  python tests/golden/make_golden.py            (small cases)
+      python tests/golden/make_golden.py --mid-size  (the L = 4096 workload)
 """
 import hashlib
 import json
@@ -17,6 +23,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import oracle as o  # noqa: E402
+from paper_1606_00310_gb300 import workloads  # noqa: E402  (seeded inputs only)
 
 CASES = [
     # L=64, p=1, q=0, seed 1, 1000 MCS, roughness at 1, 2, 4, ..., 512 (the small lattice case)
@@ -37,6 +44,15 @@ CASES = [
 ]
 
 
+# L=4096, 16.8M sites, flat start, 10^4 MCS, exact W^2 at 40 log-spaced times, dyadic
+# (3/4, 1/4), seeds 1-4 (the (1, 0) runs of this workload follow the p = 1 closed form)
+MID_SIZE_CASES = [
+    dict(name="L4096_p3/4_q1/4_s%d" % s, L=4096, seed=s, p=0.75, q=0.25, mode=1,
+         times=workloads.log_spaced_times(10_000, 40))
+    for s in (1, 4, 2, 3)
+]
+
+
 def run_case(c):
     bx, by = o.init_flat(c["L"])
     obs = []
@@ -50,11 +66,24 @@ def run_case(c):
     return {**c, "obs": obs, "final_words_sha256": hashlib.sha256(words.tobytes()).hexdigest()}
 
 
+SOURCE = "CPU oracle (oracle/sca_oracle.c); paper arXiv 1606.00310 Sec. I.A, II"
+
+
+def write(name, cases):
+    tmp = os.path.join(HERE, name + ".tmp")
+    with open(tmp, "w") as f:
+        json.dump({"source": SOURCE, "cases": cases}, f, indent=1)
+    os.replace(tmp, os.path.join(HERE, name))
+
+
 def main():
-    out = {"source": "CPU oracle (oracle/sca_oracle.c); paper arXiv 1606.00310 Sec. I.A, II",
-           "cases": [run_case(c) for c in CASES]}
-    with open(os.path.join(HERE, "oracle_small.json"), "w") as f:
-        json.dump(out, f, indent=1)
+    if "--mid-size" in sys.argv:
+        done = []
+        for c in MID_SIZE_CASES:
+            done.append(run_case(c))
+            write("oracle_mid_size.json", done)
+        return
+    write("oracle_small.json", [run_case(c) for c in CASES])
 
 
 if __name__ == "__main__":

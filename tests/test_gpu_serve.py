@@ -130,21 +130,28 @@ def test_cancel_timeout_and_bad_requests(sca):
 
 
 def test_request_stream_sample_against_oracle(sca):
-    """Requests drawn from the serving workload (non-dyadic p, q = 1 - p, 512-8192 MCS): the
-    small ones, served while larger ones from the same stream run beside them, equal the
-    oracle at every observation time."""
+    """Requests drawn from the serving workload (non-dyadic p, q = 1 - p, 512-8192 MCS): three
+    small ones and one with L = 1152 (a row length that is not a power of two), served while
+    larger ones from the same stream run beside them, equal the oracle at every observation
+    time, and their final states (returned through sca_server_submit_state) equal the
+    oracle's final words."""
     from paper_1606_00310_gb300 import workloads
     stream = workloads.request_stream(n=2000)
     small = [r for r in stream if r["L"] <= 384 and r["mcs"] <= 2000][:3]
+    mid = [r for r in stream if r["id"] == 1017]
+    assert mid[0]["L"] == 1152 and mid[0]["mcs"] == 563
+    sample = small + mid
     big = [r for r in stream if r["L"] >= 2048][:4]
     assert len(small) == 3
+    finals = [np.zeros(sca.words_count(r["L"]), np.uint32) for r in sample]
     with sca.Server(budget_bytes=16 << 30, max_active=8, max_L=8192) as srv:
         tk_big = [srv.submit(r["L"], r["p"], r["q"], r["seed"], r["mcs"]) for r in big]
-        tk_small = [srv.submit(r["L"], r["p"], r["q"], r["seed"], r["mcs"]) for r in small]
-        results = [srv.wait(tk, 300000) for tk in tk_small]
+        tk_s = [srv.submit(r["L"], r["p"], r["q"], r["seed"], r["mcs"], final_words=f)
+                for r, f in zip(sample, finals)]
+        results = [srv.wait(tk, 300000) for tk in tk_s]
         for tk in tk_big:
             srv.cancel(tk)
-    for r, (rc, obs, _) in zip(small, results):
+    for r, (rc, obs, _), fw in zip(sample, results, finals):
         assert rc == sca.OK
         bx, by = o.init_flat(r["L"])
         t = 0
@@ -153,6 +160,15 @@ def test_request_stream_sample_against_oracle(sca):
             t = x.t
             ref = o.observe(bx, by)
             assert (x.S1, x.S2, x.num) == (ref["S1"], ref["S2"], ref["num"]), (r, x.t)
+        assert t == r["mcs"]
+        assert np.array_equal(fw, o.pack(bx, by)), r
+
+
+def test_submit_state_refuses_a_short_buffer(sca):
+    with sca.Server(budget_bytes=1 << 30, max_active=1, max_L=512) as srv:
+        with pytest.raises(sca.ScaError) as e:
+            srv.submit(256, 0.5, 0.0, 1, 10, final_words=np.zeros(sca.words_count(256) - 1, np.uint32))
+        assert e.value.code == sca.EINVAL
 
 
 def test_served_kernels_agree(sca):

@@ -251,3 +251,63 @@ def test_wave01_rough_full_size(sca, L, times):
             res.append(([(g.S1, g.S2, g.num) for g in obs], sim.state_tensor().clone()))
     assert res[0][0] == res[1][0]
     assert torch.equal(res[0][1], res[1][1])
+
+
+def _band_bits(w4, L, rows):
+    """(bx, by) bytes of the given lattice rows from their canonical words w4[s][d][i][j]
+    (restating the packed layout: site k of sublattice s in row y is x = 2k + ((s + y) & 1))."""
+    bx = np.zeros((len(rows), L), np.uint8)
+    by = np.zeros((len(rows), L), np.uint8)
+    k = np.arange(L // 2)
+    for i, y in enumerate(rows):
+        for s in (0, 1):
+            x = 2 * k + ((s + y) & 1)
+            bx[i, x] = (w4[s, 0, i, k >> 5] >> (k & 31)) & 1
+            by[i, x] = (w4[s, 1, i, k >> 5] >> (k & 31)) & 1
+    return bx, by
+
+
+def _device_rows(sim, L, rows):
+    """Canonical words of the given rows, all four planes, copied from the device state."""
+    import torch
+    st = sim.state_tensor().view(2, 2, L, L // 64)
+    idx = torch.tensor(rows, dtype=torch.long, device=st.device)
+    return st.index_select(2, idx).cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("L,times,nrows,y_firsts", [(65536, [16, 40], 320, (1000, 65536 - 150)),
+                                                     (131072, [16, 33], 256, (131072 - 90,))])
+def test_headline_kernel_rough_band_against_oracle(sca, L, times, nrows, y_firsts):
+    """The benchmark's kernel (height bits, 16 MCS per launch, then the shorter launch up to the
+    last time) at the benchmark's lattice and at the largest one, checked against the oracle
+    itself on bands of rows, one of them wrapping around the periodic boundary in y.  Start: a
+    rough surface, 3 MCS of p = 5/8, q = 3/8 (seed 31) from flat, made on the GPU by the two-pass
+    kernel and by the band oracle from its own flat band (their common rows are compared too);
+    then p = 1, q = 0.  After n MCS in all, a band of the oracle holds the full lattice's rows
+    [2n, nrows - 2n) exactly (each half-step widens the dependence by one row either way)."""
+    n_rough, seed_rough = 3, 31
+    words = _rough_gpu(sca, L, n_rough, seed=seed_rough)
+    with sca.Sim(L, seed=5, p=1.0, q=0.0) as sim:
+        sim.set_state(words, t=0)
+        del words
+        assert sim.kernel_in_use() == sca.KERNEL_WAVE
+        bands = {y0: [(y0 + i) % L for i in range(nrows)] for y0 in y_firsts}
+        start = {y0: _device_rows(sim, L, rows) for y0, rows in bands.items()}
+        obs = sim.run(times)
+        assert all(g.status == 0 for g in obs)
+        final = {y0: _device_rows(sim, L, rows) for y0, rows in bands.items()}
+    for y0, rows in bands.items():
+        gx, gy = o.init_flat_band(L, y0, nrows)
+        o.run_band(L, y0, gx, gy, seed_rough, 0.625, 0.375, t0=0, n_mcs=n_rough)
+        m = 2 * n_rough
+        bx, by = _band_bits(start[y0], L, rows)
+        assert np.array_equal(bx[m:nrows - m], gx[m:nrows - m])
+        assert np.array_equal(by[m:nrows - m], gy[m:nrows - m])
+        o.run_band(L, y0, gx, gy, 5, 1.0, 0.0, t0=0, n_mcs=times[-1])
+        m = 2 * (n_rough + times[-1])
+        assert nrows - 2 * m >= 100
+        bx, by = _band_bits(final[y0], L, rows)
+        assert np.array_equal(bx[m:nrows - m], gx[m:nrows - m])
+        assert np.array_equal(by[m:nrows - m], gy[m:nrows - m])
+        # the rough start and the result differ inside the compared rows: the kernel did work
+        assert not np.array_equal(bx[m:nrows - m], _band_bits(start[y0], L, rows)[0][m:nrows - m])
