@@ -54,6 +54,29 @@ def lib():
         L.oracle_unpack.restype = None
         L.oracle_threads.argtypes = [C.c_int]
         L.oracle_threads.restype = C.c_int
+        L.oracle_init_flat_rect.argtypes = [C.c_int64, C.c_int64, u8p, u8p]
+        L.oracle_init_flat_rect.restype = None
+        L.oracle_init_flat_band_rect.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64, u8p, u8p]
+        L.oracle_init_flat_band_rect.restype = None
+        L.oracle_run_rect.argtypes = [C.c_int64, C.c_int64, u8p, u8p, C.c_uint64, C.c_double,
+                                      C.c_double, C.c_int, C.c_uint64, C.c_uint64]
+        L.oracle_run_rect.restype = C.c_int
+        L.oracle_run_band_rect.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64, u8p, u8p,
+                                           C.c_uint64, C.c_double, C.c_double, C.c_int, C.c_uint64,
+                                           C.c_uint64]
+        L.oracle_run_band_rect.restype = C.c_int
+        L.oracle_heights_rect.argtypes = [C.c_int64, C.c_int64, u8p, u8p, i64p]
+        L.oracle_heights_rect.restype = C.c_int
+        L.oracle_observe_rect.argtypes = [C.c_int64, C.c_int64, u8p, u8p, C.POINTER(C.c_int64),
+                                          u64p, u64p]
+        L.oracle_observe_rect.restype = C.c_int
+        L.oracle_pack_rect.argtypes = [C.c_int64, C.c_int64, u8p, u8p, u32p]
+        L.oracle_pack_rect.restype = None
+        L.oracle_unpack_rect.argtypes = [C.c_int64, C.c_int64, u32p, u8p, u8p]
+        L.oracle_unpack_rect.restype = None
+        L.oracle_corr_rect.argtypes = [C.c_int64, C.c_int64, u8p, u8p, u8p, u8p,
+                                       C.POINTER(C.c_int64), C.POINTER(C.c_int64), i64p, i64p]
+        L.oracle_corr_rect.restype = C.c_int
         _lib = L
     return _lib
 
@@ -75,12 +98,14 @@ def philox4x32_10(ctr, key):
     return out
 
 
-def word_draw_bit(L, seed, t, s, draw, x, y) -> int:
-    return int(lib().oracle_word_draw_bit(L, seed, t, s, draw, x, y))
+def word_draw_bit(X, seed, t, s, draw, x, y) -> int:
+    """Draw bit of site (x, y) for rows of X sites (X = L on a square lattice)."""
+    return int(lib().oracle_word_draw_bit(X, seed, t, s, draw, x, y))
 
 
-def site_uniform(L, seed, t, s, x, y) -> int:
-    return int(lib().oracle_site_uniform(L, seed, t, s, x, y))
+def site_uniform(X, seed, t, s, x, y) -> int:
+    """Per-site 32-bit uniform of site (x, y) for rows of X sites."""
+    return int(lib().oracle_site_uniform(X, seed, t, s, x, y))
 
 
 def dyadic_split(p):
@@ -169,3 +194,92 @@ def unpack(L, words):
     by = np.empty((L, L), dtype=np.uint8)
     lib().oracle_unpack(L, words, bx, by)
     return bx, by
+
+
+# ----------------------------------------------------------------------------- X x Y lattices
+# Arrays are (Y, X): Y rows of X sites.  The square functions above are the case X = Y = L.
+
+def init_flat_rect(X, Y):
+    bx = np.empty((Y, X), dtype=np.uint8)
+    by = np.empty((Y, X), dtype=np.uint8)
+    lib().oracle_init_flat_rect(X, Y, bx, by)
+    return bx, by
+
+
+def init_flat_band_rect(X, Y, y_first, nrows):
+    bx = np.empty((nrows, X), dtype=np.uint8)
+    by = np.empty((nrows, X), dtype=np.uint8)
+    lib().oracle_init_flat_band_rect(X, Y, y_first, nrows, bx, by)
+    return bx, by
+
+
+def run_rect(bx, by, seed, p, q, mode=None, t0=0, n_mcs=1):
+    Y, X = bx.shape
+    if mode is None:
+        mode = rng_mode(p, q)
+    if lib().oracle_run_rect(X, Y, bx, by, seed, float(p), float(q), mode, t0, n_mcs) != 0:
+        raise ValueError("oracle_run_rect: bad parameters")
+
+
+def run_band_rect(X, Y, y_first, bx, by, seed, p, q, mode=None, t0=0, n_mcs=1):
+    nrows = bx.shape[0]
+    if mode is None:
+        mode = rng_mode(p, q)
+    if lib().oracle_run_band_rect(X, Y, y_first, nrows, bx, by, seed, float(p), float(q), mode, t0,
+                                  n_mcs) != 0:
+        raise ValueError("oracle_run_band_rect: bad parameters")
+
+
+def heights_rect(bx, by):
+    Y, X = bx.shape
+    h = np.empty((Y, X), dtype=np.int64)
+    if lib().oracle_heights_rect(X, Y, bx, by, h) != 0:
+        raise ValueError("slopes do not close: heights are not single-valued")
+    return h
+
+
+def observe_rect(bx, by):
+    """Exact roughness sums of an X x Y lattice: dict(S1, S2, num, N), N = X*Y."""
+    Y, X = bx.shape
+    S1 = C.c_int64()
+    S2 = np.zeros(2, dtype=np.uint64)
+    num = np.zeros(2, dtype=np.uint64)
+    if lib().oracle_observe_rect(X, Y, bx, by, C.byref(S1), S2, num) != 0:
+        raise ValueError("slopes do not close: heights are not single-valued")
+    return {"S1": int(S1.value), "S2": int(S2[0]) | (int(S2[1]) << 64),
+            "num": int(num[0]) | (int(num[1]) << 64), "N": X * Y}
+
+
+def pack_rect(bx, by):
+    Y, X = bx.shape
+    w = np.empty(4 * Y * words_per_row(X), dtype=np.uint32)
+    lib().oracle_pack_rect(X, Y, bx, by, w)
+    return w
+
+
+def unpack_rect(X, Y, words):
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    assert words.size == 4 * Y * words_per_row(X)
+    bx = np.empty((Y, X), dtype=np.uint8)
+    by = np.empty((Y, X), dtype=np.uint8)
+    lib().oracle_unpack_rect(X, Y, words, bx, by)
+    return bx, by
+
+
+def corr(a, b):
+    """Two-time height correlation of states a = (ax, ay) and b = (bx, by) of one lattice:
+    dict(Sa, Sb, Sab, cnum, N) with Python ints; C = cnum / N^2 (cnum may be negative)."""
+    ax, ay = a
+    bx, by = b
+    Y, X = ax.shape
+    Sa = C.c_int64()
+    Sb = C.c_int64()
+    Sab = np.zeros(2, dtype=np.int64)
+    cn = np.zeros(2, dtype=np.int64)
+    if lib().oracle_corr_rect(X, Y, ax, ay, bx, by, C.byref(Sa), C.byref(Sb), Sab, cn) != 0:
+        raise ValueError("slopes do not close: heights are not single-valued")
+
+    def i128(v):
+        return (int(v[1]) << 64) + (int(v[0]) & 0xFFFFFFFFFFFFFFFF)
+    return {"Sa": int(Sa.value), "Sb": int(Sb.value), "Sab": i128(Sab), "cnum": i128(cn),
+            "N": X * Y}

@@ -33,8 +33,14 @@
  *   - heights: h(0,0) = 0, h(0,y) sums sy- down column 0, h(x,y) sums sx- along row y;
  *     roughness W^2 = (1/N) sum h^2 - ((1/N) sum h)^2, kept exact as num = N*S2 - S1^2.
  *
+ * Lattice: X sites per row (x = 0..X-1) and Y rows (y = 0..Y-1), both even, periodic in both
+ * directions (Sec. II.B names the lateral sizes X and Y; its benchmarks use X = Y = L, and its
+ * wide-system variant X >= 2^17).  The functions without the _rect suffix are the square case
+ * X = Y = L.  Everything that depends on the row length (the packed layout, the random-number
+ * unit of a site) takes X; rows only enter through y and its periodic successor.
+ *
  * Canonical packed layout (the only state format exchanged with the library):
- *   W = ceil(L/64) 32-bit words per sublattice row; word index ((s*2 + d)*L + y)*W + j for
+ *   W = ceil(X/64) 32-bit words per sublattice row; word index ((s*2 + d)*Y + y)*W + j for
  *   sublattice s, direction d (0 = x, 1 = y), row y; bit b of word j is sublattice site
  *   k = 32*j + b, which is lattice site x = 2k + ((s + y) & 1).
  */
@@ -88,23 +94,25 @@ static uint32_t philox_lane(uint64_t seed, uint64_t unit, uint64_t t, int s, int
     return out[unit & 3];
 }
 
-/* Words per sublattice row in the packed layout. */
-static uint64_t words_per_row(int64_t L) { return (uint64_t)((L / 2 + 31) / 32); }
+/* Words per sublattice row in the packed layout (X sites per row). */
+static uint64_t words_per_row(int64_t X) { return (uint64_t)((X / 2 + 31) / 32); }
 
-/* Draw `draw` of the packed-word stream, bit of site (x,y) in sublattice s at MCS t. */
-uint32_t oracle_word_draw_bit(int64_t L, uint64_t seed, uint64_t t, int s, int draw,
+/* Draw `draw` of the packed-word stream, bit of site (x,y) in sublattice s at MCS t, for rows
+ * of X sites (unit = y * W + word of the site). */
+uint32_t oracle_word_draw_bit(int64_t X, uint64_t seed, uint64_t t, int s, int draw,
                               int64_t x, int64_t y)
 {
     uint64_t k = (uint64_t)(x >> 1);
-    uint64_t unit = (uint64_t)y * words_per_row(L) + (k >> 5);
+    uint64_t unit = (uint64_t)y * words_per_row(X) + (k >> 5);
     return (philox_lane(seed, unit, t, s, draw, 0) >> (k & 31)) & 1u;
 }
 
-/* Per-site 32-bit uniform of site (x,y) in sublattice s at MCS t. */
-uint32_t oracle_site_uniform(int64_t L, uint64_t seed, uint64_t t, int s, int64_t x, int64_t y)
+/* Per-site 32-bit uniform of site (x,y) in sublattice s at MCS t, for rows of X sites
+ * (unit = y * X/2 + sublattice index of the site). */
+uint32_t oracle_site_uniform(int64_t X, uint64_t seed, uint64_t t, int s, int64_t x, int64_t y)
 {
     uint64_t k = (uint64_t)(x >> 1);
-    uint64_t unit = (uint64_t)y * (uint64_t)(L / 2) + k;
+    uint64_t unit = (uint64_t)y * (uint64_t)(X / 2) + k;
     return philox_lane(seed, unit, t, s, 1, 1);
 }
 
@@ -134,7 +142,7 @@ static int dyadic_accept(uint64_t P, int n, const uint32_t *draw_bits)
 }
 
 typedef struct {
-    int64_t L;
+    int64_t L;           /* row length X (the random-number unit of a site depends on it) */
     uint64_t seed;
     int mode;            /* 1 = dyadic (packed-word draws), 2 = per-site 32-bit uniform */
     uint64_t Pp, Pq;     /* dyadic numerators */
@@ -175,16 +183,17 @@ static int accepted(const rule_t *r, uint64_t t, int s, int64_t x, int64_t y, in
     }
 }
 
-/* One attempted update of site (x,y) per Eq. (1); bx/by hold sx- / sy- bits row-major.
- * Rows are addressed through `row` so that the band variant below can reuse the rule. */
-static void update_site(const rule_t *r, uint8_t *bx, uint8_t *by, int64_t L,
+/* One attempted update of site (x,y) per Eq. (1); bx/by hold sx- / sy- bits row-major with X
+ * sites per row.  Rows are addressed through `row` so that the band variant below can reuse
+ * the rule. */
+static void update_site(const rule_t *r, uint8_t *bx, uint8_t *by, int64_t X,
                         int64_t row, int64_t row_next, int64_t x, int64_t y, uint64_t t, int s)
 {
-    int64_t xr = (x + 1) % L;
-    uint8_t *a = &bx[row * L + x];        /* sx-(x,y)            */
-    uint8_t *b = &by[row * L + x];        /* sy-(x,y)            */
-    uint8_t *c = &bx[row * L + xr];       /* sx+(x,y)=sx-(x+1,y) */
-    uint8_t *d = &by[row_next * L + x];   /* sy+(x,y)=sy-(x,y+1) */
+    int64_t xr = (x + 1) % X;
+    uint8_t *a = &bx[row * X + x];        /* sx-(x,y)            */
+    uint8_t *b = &by[row * X + x];        /* sy-(x,y)            */
+    uint8_t *c = &bx[row * X + xr];       /* sx+(x,y)=sx-(x+1,y) */
+    uint8_t *d = &by[row_next * X + x];   /* sy+(x,y)=sy-(x,y+1) */
     int is_min = (*a == 0 && *b == 0 && *c == 1 && *d == 1);
     int is_max = (*a == 1 && *b == 1 && *c == 0 && *d == 0);
     if ((is_min && accepted(r, t, s, x, y, 0)) || (is_max && accepted(r, t, s, x, y, 1))) {
@@ -193,109 +202,135 @@ static void update_site(const rule_t *r, uint8_t *bx, uint8_t *by, int64_t L,
 }
 
 /* Flat initial surface h(x,y) = (x + y) & 1: sx-(x,y) = h(x,y) - h(x-1,y) is -1 on even
- * sites and +1 on odd sites (L even), likewise sy-. */
-void oracle_init_flat(int64_t L, uint8_t *bx, uint8_t *by)
+ * sites and +1 on odd sites (X, Y even), likewise sy-. */
+void oracle_init_flat_rect(int64_t X, int64_t Y, uint8_t *bx, uint8_t *by)
 {
-    for (int64_t y = 0; y < L; y++)
-        for (int64_t x = 0; x < L; x++) {
+    for (int64_t y = 0; y < Y; y++)
+        for (int64_t x = 0; x < X; x++) {
             uint8_t v = (uint8_t)((x + y) & 1);
-            bx[y * L + x] = v;
-            by[y * L + x] = v;
+            bx[y * X + x] = v;
+            by[y * X + x] = v;
         }
 }
 
-/* Run n_mcs Monte-Carlo steps starting at MCS index t0 (Sec. I.A schedule).  Returns 0, or
- * -1 on bad parameters. */
-int oracle_run(int64_t L, uint8_t *bx, uint8_t *by, uint64_t seed, double p, double q,
-               int mode, uint64_t t0, uint64_t n_mcs)
+void oracle_init_flat(int64_t L, uint8_t *bx, uint8_t *by) { oracle_init_flat_rect(L, L, bx, by); }
+
+/* Run n_mcs Monte-Carlo steps starting at MCS index t0 (Sec. I.A schedule) on the X x Y
+ * lattice.  Returns 0, or -1 on bad parameters. */
+int oracle_run_rect(int64_t X, int64_t Y, uint8_t *bx, uint8_t *by, uint64_t seed, double p,
+                    double q, int mode, uint64_t t0, uint64_t n_mcs)
 {
     rule_t r;
-    if (L < 2 || (L & 1)) return -1;
-    if (rule_make(&r, L, seed, p, q, mode)) return -1;
+    if (X < 2 || (X & 1) || Y < 2 || (Y & 1)) return -1;
+    if (rule_make(&r, X, seed, p, q, mode)) return -1;
     for (uint64_t t = t0; t < t0 + n_mcs; t++) {
         for (int s = 0; s <= 1; s++) {
             #pragma omp parallel for schedule(static)
-            for (int64_t y = 0; y < L; y++)
-                for (int64_t x = 0; x < L; x++)
+            for (int64_t y = 0; y < Y; y++)
+                for (int64_t x = 0; x < X; x++)
                     if (((x + y) & 1) == s)
-                        update_site(&r, bx, by, L, y, (y + 1) % L, x, y, t, s);
+                        update_site(&r, bx, by, X, y, (y + 1) % Y, x, y, t, s);
         }
     }
     return 0;
 }
 
+int oracle_run(int64_t L, uint8_t *bx, uint8_t *by, uint64_t seed, double p, double q,
+               int mode, uint64_t t0, uint64_t n_mcs)
+{
+    return oracle_run_rect(L, L, bx, by, seed, p, q, mode, t0, n_mcs);
+}
+
 /* The same dynamics on a band of `nrows` consecutive lattice rows starting at global row
- * y_first (taken mod L), full width L.  Only rows whose successor is inside the band are
+ * y_first (taken mod Y), full width X.  Only rows whose successor is inside the band are
  * updated, so after n MCS the band rows [2n, nrows - 2n) hold exactly the full lattice's rows
  * (an update at row y reads rows y and y+1 and writes them, so each half-step widens the
  * dependence by one row either way).  Used to check samples of lattices too large to hold. */
-int oracle_run_band(int64_t L, int64_t y_first, int64_t nrows, uint8_t *bx, uint8_t *by,
-                    uint64_t seed, double p, double q, int mode, uint64_t t0, uint64_t n_mcs)
+int oracle_run_band_rect(int64_t X, int64_t Y, int64_t y_first, int64_t nrows, uint8_t *bx,
+                         uint8_t *by, uint64_t seed, double p, double q, int mode, uint64_t t0,
+                         uint64_t n_mcs)
 {
     rule_t r;
-    if (L < 2 || (L & 1) || nrows < 2) return -1;
-    if (rule_make(&r, L, seed, p, q, mode)) return -1;
+    if (X < 2 || (X & 1) || Y < 2 || (Y & 1) || nrows < 2) return -1;
+    if (rule_make(&r, X, seed, p, q, mode)) return -1;
     for (uint64_t t = t0; t < t0 + n_mcs; t++) {
         for (int s = 0; s <= 1; s++) {
             #pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < nrows - 1; i++) {
-                int64_t y = (y_first + i) % L;
-                for (int64_t x = 0; x < L; x++)
+                int64_t y = (y_first + i) % Y;
+                for (int64_t x = 0; x < X; x++)
                     if (((x + y) & 1) == s)
-                        update_site(&r, bx, by, L, i, i + 1, x, y, t, s);
+                        update_site(&r, bx, by, X, i, i + 1, x, y, t, s);
             }
         }
     }
     return 0;
 }
 
+int oracle_run_band(int64_t L, int64_t y_first, int64_t nrows, uint8_t *bx, uint8_t *by,
+                    uint64_t seed, double p, double q, int mode, uint64_t t0, uint64_t n_mcs)
+{
+    return oracle_run_band_rect(L, L, y_first, nrows, bx, by, seed, p, q, mode, t0, n_mcs);
+}
+
 /* Flat start for a band (global row coordinates). */
-void oracle_init_flat_band(int64_t L, int64_t y_first, int64_t nrows, uint8_t *bx, uint8_t *by)
+void oracle_init_flat_band_rect(int64_t X, int64_t Y, int64_t y_first, int64_t nrows, uint8_t *bx,
+                                uint8_t *by)
 {
     for (int64_t i = 0; i < nrows; i++) {
-        int64_t y = (y_first + i) % L;
-        for (int64_t x = 0; x < L; x++) {
+        int64_t y = (y_first + i) % Y;
+        for (int64_t x = 0; x < X; x++) {
             uint8_t v = (uint8_t)((x + y) & 1);
-            bx[i * L + x] = v;
-            by[i * L + x] = v;
+            bx[i * X + x] = v;
+            by[i * X + x] = v;
         }
     }
 }
 
-/* Heights of the whole lattice (small L): h(0,0) = 0, down column 0 with sy-, then along
+void oracle_init_flat_band(int64_t L, int64_t y_first, int64_t nrows, uint8_t *bx, uint8_t *by)
+{
+    oracle_init_flat_band_rect(L, L, y_first, nrows, bx, by);
+}
+
+/* Heights of the whole lattice (small sizes): h(0,0) = 0, down column 0 with sy-, then along
  * each row with sx-.  Returns 0, or -1 if the slopes do not close around a torus cycle
  * (heights would not be single-valued). */
-int oracle_heights(int64_t L, const uint8_t *bx, const uint8_t *by, int64_t *h)
+int oracle_heights_rect(int64_t X, int64_t Y, const uint8_t *bx, const uint8_t *by, int64_t *h)
 {
     int64_t h0 = 0;
-    for (int64_t y = 0; y < L; y++) {
-        if (y > 0) h0 += 2 * (int64_t)by[y * L + 0] - 1;
+    for (int64_t y = 0; y < Y; y++) {
+        if (y > 0) h0 += 2 * (int64_t)by[y * X + 0] - 1;
         int64_t hx = h0;
-        h[y * L + 0] = hx;
-        for (int64_t x = 1; x < L; x++) {
-            hx += 2 * (int64_t)bx[y * L + x] - 1;
-            h[y * L + x] = hx;
+        h[y * X + 0] = hx;
+        for (int64_t x = 1; x < X; x++) {
+            hx += 2 * (int64_t)bx[y * X + x] - 1;
+            h[y * X + x] = hx;
         }
-        if (hx + 2 * (int64_t)bx[y * L + 0] - 1 != h0) return -1;
+        if (hx + 2 * (int64_t)bx[y * X + 0] - 1 != h0) return -1;
     }
     if (h0 + 2 * (int64_t)by[0] - 1 != 0) return -1;
     return 0;
 }
 
+int oracle_heights(int64_t L, const uint8_t *bx, const uint8_t *by, int64_t *h)
+{
+    return oracle_heights_rect(L, L, bx, by, h);
+}
+
 /* Exact roughness sums.  S1 = sum h, S2 = sum h^2 (128-bit), num = N*S2 - S1^2 (128-bit,
- * never negative).  Heights are built one row at a time as in oracle_heights.  Returns 0, or
- * -1 if a row or column 0 does not close. */
-int oracle_observe(int64_t L, const uint8_t *bx, const uint8_t *by,
-                   int64_t *S1_out, uint64_t S2_out[2], uint64_t num_out[2])
+ * never negative) with N = X*Y.  Heights are built one row at a time as in
+ * oracle_heights_rect.  Returns 0, or -1 if a row or column 0 does not close. */
+int oracle_observe_rect(int64_t X, int64_t Y, const uint8_t *bx, const uint8_t *by,
+                        int64_t *S1_out, uint64_t S2_out[2], uint64_t num_out[2])
 {
     __int128 S1 = 0;
     unsigned __int128 S2 = 0;
     int bad = 0;
     int64_t h0 = 0;
-    int64_t *col0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
+    int64_t *col0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)Y);
     if (!col0) return -1;
-    for (int64_t y = 0; y < L; y++) {
-        if (y > 0) h0 += 2 * (int64_t)by[y * L + 0] - 1;
+    for (int64_t y = 0; y < Y; y++) {
+        if (y > 0) h0 += 2 * (int64_t)by[y * X + 0] - 1;
         col0[y] = h0;
     }
     if (h0 + 2 * (int64_t)by[0] - 1 != 0) bad = 1;
@@ -305,16 +340,16 @@ int oracle_observe(int64_t L, const uint8_t *bx, const uint8_t *by,
         unsigned __int128 s2 = 0;
         int rowbad = 0;
         #pragma omp for schedule(static)
-        for (int64_t y = 0; y < L; y++) {
+        for (int64_t y = 0; y < Y; y++) {
             int64_t hx = col0[y];
             s1 += hx;
             s2 += (unsigned __int128)((__int128)hx * hx);
-            for (int64_t x = 1; x < L; x++) {
-                hx += 2 * (int64_t)bx[y * L + x] - 1;
+            for (int64_t x = 1; x < X; x++) {
+                hx += 2 * (int64_t)bx[y * X + x] - 1;
                 s1 += hx;
                 s2 += (unsigned __int128)((__int128)hx * hx);
             }
-            if (hx + 2 * (int64_t)bx[y * L + 0] - 1 != col0[y]) rowbad = 1;
+            if (hx + 2 * (int64_t)bx[y * X + 0] - 1 != col0[y]) rowbad = 1;
         }
         #pragma omp critical
         {
@@ -324,7 +359,7 @@ int oracle_observe(int64_t L, const uint8_t *bx, const uint8_t *by,
         }
     }
     free(col0);
-    unsigned __int128 N = (unsigned __int128)((uint64_t)L * (uint64_t)L);
+    unsigned __int128 N = (unsigned __int128)((uint64_t)X * (uint64_t)Y);
     unsigned __int128 num = N * S2 - (unsigned __int128)(S1 * S1);
     *S1_out = (int64_t)S1;
     S2_out[0] = (uint64_t)S2; S2_out[1] = (uint64_t)(S2 >> 64);
@@ -332,36 +367,85 @@ int oracle_observe(int64_t L, const uint8_t *bx, const uint8_t *by,
     return bad ? -1 : 0;
 }
 
-/* Byte arrays -> canonical packed words (4 * L * W words, zero padding bits). */
-void oracle_pack(int64_t L, const uint8_t *bx, const uint8_t *by, uint32_t *words)
+int oracle_observe(int64_t L, const uint8_t *bx, const uint8_t *by,
+                   int64_t *S1_out, uint64_t S2_out[2], uint64_t num_out[2])
 {
-    uint64_t W = words_per_row(L);
-    memset(words, 0, sizeof(uint32_t) * 4 * (size_t)L * W);
-    for (int64_t y = 0; y < L; y++)
-        for (int64_t x = 0; x < L; x++) {
+    return oracle_observe_rect(L, L, bx, by, S1_out, S2_out, num_out);
+}
+
+/* Two-time height correlation of two states of the same X x Y lattice (the paper's two-time
+ * functions and aging studies, Sec. I and Sec. IV; definition here): with heights h_a, h_b of
+ * the two states (each from h(0,0) = 0, as in oracle_heights_rect),
+ *   Sa = sum h_a, Sb = sum h_b, Sab = sum h_a h_b (128-bit),
+ *   cnum = N * Sab - Sa * Sb (signed 128-bit), C = cnum / N^2,
+ * the covariance of the two height fields over the sites, unchanged by a constant shift of
+ * either field (so the unknown absolute heights do not enter).  C(t, t) = W^2(t).
+ * Returns 0, or -1 if either state does not close. */
+int oracle_corr_rect(int64_t X, int64_t Y, const uint8_t *ax, const uint8_t *ay, const uint8_t *bx,
+                     const uint8_t *by, int64_t *Sa_out, int64_t *Sb_out, int64_t Sab_out[2],
+                     int64_t cnum_out[2])
+{
+    size_t n = (size_t)X * (size_t)Y;
+    int64_t *ha = (int64_t *)malloc(sizeof(int64_t) * n);
+    int64_t *hb = (int64_t *)malloc(sizeof(int64_t) * n);
+    if (!ha || !hb) { free(ha); free(hb); return -1; }
+    int bad = oracle_heights_rect(X, Y, ax, ay, ha) != 0 || oracle_heights_rect(X, Y, bx, by, hb) != 0;
+    __int128 Sa = 0, Sb = 0, Sab = 0;
+    for (size_t i = 0; i < n; i++) {
+        Sa += ha[i];
+        Sb += hb[i];
+        Sab += (__int128)ha[i] * hb[i];
+    }
+    free(ha);
+    free(hb);
+    __int128 cnum = (__int128)n * Sab - Sa * Sb;
+    *Sa_out = (int64_t)Sa;
+    *Sb_out = (int64_t)Sb;
+    Sab_out[0] = (int64_t)(uint64_t)Sab; Sab_out[1] = (int64_t)(Sab >> 64);
+    cnum_out[0] = (int64_t)(uint64_t)cnum; cnum_out[1] = (int64_t)(cnum >> 64);
+    return bad ? -1 : 0;
+}
+
+/* Byte arrays -> canonical packed words (4 * Y * W words, zero padding bits). */
+void oracle_pack_rect(int64_t X, int64_t Y, const uint8_t *bx, const uint8_t *by, uint32_t *words)
+{
+    uint64_t W = words_per_row(X);
+    memset(words, 0, sizeof(uint32_t) * 4 * (size_t)Y * W);
+    for (int64_t y = 0; y < Y; y++)
+        for (int64_t x = 0; x < X; x++) {
             int s = (int)((x + y) & 1);
             uint64_t k = (uint64_t)(x >> 1);
             for (int d = 0; d < 2; d++) {
-                uint8_t v = d == 0 ? bx[y * L + x] : by[y * L + x];
-                uint64_t idx = ((uint64_t)(s * 2 + d) * (uint64_t)L + (uint64_t)y) * W + (k >> 5);
+                uint8_t v = d == 0 ? bx[y * X + x] : by[y * X + x];
+                uint64_t idx = ((uint64_t)(s * 2 + d) * (uint64_t)Y + (uint64_t)y) * W + (k >> 5);
                 words[idx] |= (uint32_t)v << (k & 31);
             }
         }
 }
 
-/* Canonical packed words -> byte arrays. */
-void oracle_unpack(int64_t L, const uint32_t *words, uint8_t *bx, uint8_t *by)
+void oracle_pack(int64_t L, const uint8_t *bx, const uint8_t *by, uint32_t *words)
 {
-    uint64_t W = words_per_row(L);
-    for (int64_t y = 0; y < L; y++)
-        for (int64_t x = 0; x < L; x++) {
+    oracle_pack_rect(L, L, bx, by, words);
+}
+
+/* Canonical packed words -> byte arrays. */
+void oracle_unpack_rect(int64_t X, int64_t Y, const uint32_t *words, uint8_t *bx, uint8_t *by)
+{
+    uint64_t W = words_per_row(X);
+    for (int64_t y = 0; y < Y; y++)
+        for (int64_t x = 0; x < X; x++) {
             int s = (int)((x + y) & 1);
             uint64_t k = (uint64_t)(x >> 1);
-            uint64_t ix = ((uint64_t)(s * 2 + 0) * (uint64_t)L + (uint64_t)y) * W + (k >> 5);
-            uint64_t iy = ((uint64_t)(s * 2 + 1) * (uint64_t)L + (uint64_t)y) * W + (k >> 5);
-            bx[y * L + x] = (uint8_t)((words[ix] >> (k & 31)) & 1u);
-            by[y * L + x] = (uint8_t)((words[iy] >> (k & 31)) & 1u);
+            uint64_t ix = ((uint64_t)(s * 2 + 0) * (uint64_t)Y + (uint64_t)y) * W + (k >> 5);
+            uint64_t iy = ((uint64_t)(s * 2 + 1) * (uint64_t)Y + (uint64_t)y) * W + (k >> 5);
+            bx[y * X + x] = (uint8_t)((words[ix] >> (k & 31)) & 1u);
+            by[y * X + x] = (uint8_t)((words[iy] >> (k & 31)) & 1u);
         }
+}
+
+void oracle_unpack(int64_t L, const uint32_t *words, uint8_t *bx, uint8_t *by)
+{
+    oracle_unpack_rect(L, L, words, bx, by);
 }
 
 #ifdef _OPENMP

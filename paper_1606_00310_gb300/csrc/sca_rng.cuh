@@ -11,33 +11,14 @@ namespace sca {
 
 struct Ctr4 { uint32_t x, y, z, w; };
 
-#ifndef SCA_PHILOX_WIDE
-#define SCA_PHILOX_WIDE 0
-#endif
-
-// One 32x32 -> 64 product of a Philox round, split into its low and high words: either as
-// one wide multiply (a single instruction writing a register pair) or as a low product and a
-// separate high product.
-__device__ __forceinline__ void philox_mul(uint32_t M, uint32_t a, uint32_t &lo, uint32_t &hi)
-{
-#if SCA_PHILOX_WIDE
-    uint64_t d;
-    asm("mul.wide.u32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(M));
-    lo = (uint32_t)d;
-    hi = (uint32_t)(d >> 32);
-#else
-    lo = M * a;
-    hi = __umulhi(M, a);
-#endif
-}
-
 __device__ __forceinline__ Ctr4 philox4x32_10(Ctr4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        uint32_t lo0, hi0, lo1, hi1;
-        philox_mul(0xD2511F53u, c.x, lo0, hi0);
-        philox_mul(0xCD9E8D57u, c.z, lo1, hi1);
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
         c = Ctr4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
@@ -52,9 +33,10 @@ __device__ __forceinline__ Ctr4 philox4x32_10_rk(Ctr4 c, const uint32_t *rk)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        uint32_t lo0, hi0, lo1, hi1;
-        philox_mul(0xD2511F53u, c.x, lo0, hi0);
-        philox_mul(0xCD9E8D57u, c.z, lo1, hi1);
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
         c = Ctr4{hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0};
     }
     return c;
@@ -82,7 +64,6 @@ struct Rule {
     uint32_t Pp, Pq;      // dyadic odd numerators (p = Pp / 2^np); 0/1 when n = 0
     uint64_t Tp, Tq;      // per-site thresholds floor(p * 2^32), floor(q * 2^32)
     uint32_t rk[20];      // Philox round keys (see philox4x32_10_rk)
-    uint32_t one, two;    // the integers 1 and 2 as run-time operands (see below_mask)
 };
 
 // xi words for V consecutive packed words starting at word unit u0 (= y * W + j) of
@@ -186,82 +167,35 @@ __device__ __forceinline__ void xi_dyadic_any(const Rule &R, const uint32_t *rk,
     else xi_dyadic_fixed<V, ND>(R, rk, u0, t, s, xp, xq);
 }
 
-#ifndef SCA_UNIFORM_FMA
-#define SCA_UNIFORM_FMA 0
-#endif
-
-// All ones exactly when u < T (0 <= T <= 2^32): the high word of u * 1 + (2^64 - T), one wide
-// integer multiply-add.  The multiply-add runs on the multiply (FMA) pipe, which the Philox
-// rounds leave half idle, instead of a compare and a select on the logic (ALU) pipe, which
-// they keep busy with their XORs.  `one` is the rule's run-time 1, so the compiler keeps the
-// multiply-add instead of turning it into an addition on the ALU pipe.
-__device__ __forceinline__ uint32_t below_mask(uint32_t u, uint32_t one, uint64_t negT)
-{
-    uint64_t d;
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(u), "r"(one), "l"(negT));
-    return (uint32_t)(d >> 32);
-}
-
-// acc * 2 + m (mod 2^32), an integer multiply-add with the rule's run-time 2.
-__device__ __forceinline__ uint32_t shift_in(uint32_t acc, uint32_t two, uint32_t m)
-{
-    uint32_t d;
-    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(acc), "r"(two), "r"(m));
-    return d;
-}
-
 // xi words for one packed word from per-site uniforms (Sec. II.B: one random number per
 // site).  Site unit u = y * (L/2) + k, k = 32 * word + bit; four sites per Philox call.  All
 // eight calls of a word are made (skipping ineligible groups would diverge within a warp and
-// save nothing); they run four at a time as independent chains.
-//
-// A threshold's word is built either with compares (thresholds as 32 bits, p = 1 carried by
-// an all-ones mask) or on the multiply pipe: each site's below_mask (0 or all ones) is shifted
-// in, last site first, by acc = 2 acc + m, so that after the 16 sites of a half acc is minus
-// the half's mask (mod 2^32); SCA_UNIFORM_FMA = 1 takes deposition (p) that way and removal
-// (q) with compares, 2 takes both that way.
+// save nothing); they run four at a time as independent chains.  Thresholds are 32-bit, with
+// p = 1 (threshold 2^32) carried by the all_p / all_q masks.
 __device__ __forceinline__ void xi_uniform_word(const Rule &R, const uint32_t *rk, uint64_t site0,
                                                 uint64_t t, int s, uint32_t need, uint32_t &xp,
                                                 uint32_t &xq)
 {
     (void)need;
-    constexpr bool P_FMA = SCA_UNIFORM_FMA >= 1, Q_FMA = SCA_UNIFORM_FMA >= 2;
     const uint32_t Tp = R.Tp >= (1ull << 32) ? 0xFFFFFFFFu : (uint32_t)R.Tp;
     const uint32_t Tq = R.Tq >= (1ull << 32) ? 0xFFFFFFFFu : (uint32_t)R.Tq;
     const uint32_t all_p = R.Tp >= (1ull << 32) ? 0xFFFFFFFFu : 0u;
     const uint32_t all_q = R.Tq >= (1ull << 32) ? 0xFFFFFFFFu : 0u;
-    const uint64_t nTp = 0ull - R.Tp, nTq = 0ull - R.Tq;
-    xp = P_FMA ? 0u : all_p;
-    xq = Q_FMA ? 0u : all_q;
+    xp = all_p;
+    xq = all_q;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         Ctr4 o[4];
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             o[g] = philox4x32_10_rk(draw_counter((site0 >> 2) + 4 * half + g, t, s, 1, 1), rk);
-        if (P_FMA || Q_FMA) {
-            uint32_t ap = 0u, aq = 0u;
-#pragma unroll
-            for (int g = 3; g >= 0; --g) {
-                const uint32_t u[4] = {o[g].x, o[g].y, o[g].z, o[g].w};
-#pragma unroll
-                for (int c = 3; c >= 0; --c) {
-                    if (P_FMA) ap = shift_in(ap, R.two, below_mask(u[c], R.one, nTp));
-                    if (Q_FMA) aq = shift_in(aq, R.two, below_mask(u[c], R.one, nTq));
-                }
-            }
-            if (P_FMA) xp -= ap << (16 * half);
-            if (Q_FMA) xq -= aq << (16 * half);
-        }
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             const int b = 16 * half + 4 * g;
-            if (!P_FMA)
-                xp |= ((uint32_t)(o[g].x < Tp) << b) | ((uint32_t)(o[g].y < Tp) << (b + 1)) |
-                      ((uint32_t)(o[g].z < Tp) << (b + 2)) | ((uint32_t)(o[g].w < Tp) << (b + 3));
-            if (!Q_FMA)
-                xq |= ((uint32_t)(o[g].x < Tq) << b) | ((uint32_t)(o[g].y < Tq) << (b + 1)) |
-                      ((uint32_t)(o[g].z < Tq) << (b + 2)) | ((uint32_t)(o[g].w < Tq) << (b + 3));
+            xp |= ((uint32_t)(o[g].x < Tp) << b) | ((uint32_t)(o[g].y < Tp) << (b + 1)) |
+                  ((uint32_t)(o[g].z < Tp) << (b + 2)) | ((uint32_t)(o[g].w < Tp) << (b + 3));
+            xq |= ((uint32_t)(o[g].x < Tq) << b) | ((uint32_t)(o[g].y < Tq) << (b + 1)) |
+                  ((uint32_t)(o[g].z < Tq) << (b + 2)) | ((uint32_t)(o[g].w < Tq) << (b + 3));
         }
     }
 }

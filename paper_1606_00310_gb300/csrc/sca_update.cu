@@ -49,18 +49,9 @@ struct HalfArgs {
     Rule R;
 };
 
-#ifndef SCA_HALF_MAXNREG
-#define SCA_HALF_MAXNREG 0
-#endif
-#if SCA_HALF_MAXNREG
-#define SCA_HALF_BOUNDS __maxnreg__(SCA_HALF_MAXNREG)
-#else
-#define SCA_HALF_BOUNDS __launch_bounds__(512)
-#endif
-
 // MODE 0: p, q in {0,1}; 1: dyadic draws; 2: per-site uniform draws.
 template <int V, int MODE>
-__global__ void SCA_HALF_BOUNDS k_half_step(const HalfArgs a)
+__global__ void __launch_bounds__(512) k_half_step(const HalfArgs a)
 {
     extern __shared__ uint32_t sh[];
     const int tpb = blockDim.x / a.TP;                  // teams per block
@@ -201,26 +192,11 @@ static cudaError_t launch_half_v(const HalfArgs &a, const TeamShape &ts, cudaStr
     return cudaGetLastError();
 }
 
-#ifndef SCA_HALF_UNIFORM_V
-#define SCA_HALF_UNIFORM_V 4
-#endif
-
 cudaError_t launch_half_step(uint32_t *A, uint32_t L, uint64_t t, int s, const Rule &R,
                              cudaStream_t st, const uint64_t *t_dev)
 {
     const uint32_t W = L / 64;
-    TeamShape ts = team_shape(W, 256);
-    if (R.mode == 2 && ts.V > SCA_HALF_UNIFORM_V) {
-        // per-site uniforms: fewer words per thread (more resident warps)
-        TeamShape t2;
-        t2.V = SCA_HALF_UNIFORM_V;
-        t2.T = (int)(W / t2.V);
-        t2.TP = t2.T <= 32 ? 1 : (t2.T + 31) / 32 * 32;
-        if (t2.T <= 32) while (t2.TP < t2.T) t2.TP <<= 1;
-        t2.teams = t2.TP >= 256 ? 1 : 256 / t2.TP;
-        t2.block = t2.teams * t2.TP;
-        if (t2.block <= 512) ts = t2;
-    }
+    const TeamShape ts = team_shape(W, 256);
     HalfArgs a{A, L, W, t, t_dev, s, ts.T, ts.TP, R};
     const int mode = (int)R.mode;
 #define SCA_HALF(VV)                                                        \

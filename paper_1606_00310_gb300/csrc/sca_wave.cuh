@@ -61,9 +61,6 @@ constexpr uint32_t kWaveTileWords = 30; // words a warp tile owns (32 lanes minu
 #ifndef SCA_WAVE_MINB
 #define SCA_WAVE_MINB 16
 #endif
-#ifndef SCA_WAVE_XI_FIRST
-#define SCA_WAVE_XI_FIRST 0
-#endif
 #ifndef SCA_WAVE_P0
 #define SCA_WAVE_P0 SCA_WAVE_U0
 #endif
@@ -265,31 +262,8 @@ __device__ __forceinline__ void wave_half_steps(const Rule &Rl, uint32_t (&h)[2 
     // rows of sublattice s at parity (s + y) & 1 == 1 sit one site right; for every half-step
     // of this position (s + y) & 1 == (R + 1) & 1, and the first row of a block is even
     const bool right_shift = ((u + 1) & 1) != 0;
-#if SCA_WAVE_XI_FIRST
-    // the draws of the 2K half-steps of this position depend only on (row, MCS, sublattice):
-    // make them in groups of G half-steps, as independent chains, ahead of the updates
-    constexpr int G = SCA_WAVE_XI_FIRST < S ? SCA_WAVE_XI_FIRST : S;
-    uint32_t xpa[MODE == 1 ? G : 1][V], xqa[MODE == 1 ? G : 1][V];
-#endif
 #pragma unroll
     for (int i = 1; i <= S; ++i) {
-#if SCA_WAVE_XI_FIRST
-        if constexpr (MODE == 1) {
-            if ((i - 1) % G == 0) {
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    const int ii = i + g, sg = (ii - 1) & 1;
-                    const uint32_t y = yu >= (uint32_t)ii ? yu - (uint32_t)ii : yu + L - (uint32_t)ii;
-                    const KeysRk key{Rl.rk};
-                    if constexpr (ND == 0)
-                        wave_xi<V>(Rl, key, (uint64_t)y * W + j, t0 + (uint32_t)((ii - 1) >> 1), sg, xpa[g], xqa[g]);
-                    else
-                        wave_xi_fixed<V, ND, DP, DQ>(Rl, key, (uint64_t)y * W + j, t0 + (uint32_t)((ii - 1) >> 1), sg,
-                                                     xpa[g], xqa[g]);
-                }
-            }
-        }
-#endif
         const int s = (i - 1) & 1, ns = s ^ 1;
         const int c = base + u - i;             // slot of row R - i
         uint32_t(&b)[V] = h[c][s];
@@ -320,20 +294,12 @@ __device__ __forceinline__ void wave_half_steps(const Rule &Rl, uint32_t (&h)[2 
                                 0u, xp[v], xq[v]);
         }
         if constexpr (MODE == 1) {
-#if SCA_WAVE_XI_FIRST
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                xp[v] = xpa[(i - 1) % G][v];
-                xq[v] = xqa[(i - 1) % G][v];
-            }
-#else
             const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
             const KeysRk key{Rl.rk};
             if constexpr (ND == 0)
                 wave_xi<V>(Rl, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
             else
                 wave_xi_fixed<V, ND, DP, DQ>(Rl, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
-#endif
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
