@@ -15,18 +15,19 @@
  *     host results synchronise it.
  *   - Types are plain C; no PyTorch or CUDA types appear in the signatures.
  *
- * Model (paper Sec. I.A, Eq. 1): slopes sx-, sy- in {-1,+1} per site of an L x L periodic
- * lattice; a local minimum (sx-, sx+, sy-, sy+) = (-1, +1, -1, +1) turns into the maximum
+ * Model (paper Sec. I.A, Eq. 1): slopes sx-, sy- in {-1,+1} per site of an X x Y periodic
+ * lattice (X = L sites per row, Y rows; Y = L unless sca_params.Ly says otherwise, Sec. II.B
+ * names the two lateral sizes); a local minimum (sx-, sx+, sy-, sy+) = (-1, +1, -1, +1) turns into the maximum
  * (+1, -1, +1, -1) with probability p (deposition) and back with probability q (removal).
  * One Monte-Carlo step (MCS) updates every even site ((x + y) & 1 == 0), then every odd site.
  *
  * State format (the only one that crosses this ABI): the "canonical packed words".  A slope
  * -1 is bit 0, +1 is bit 1 (paper Sec. II.A); sx-(x,y) = h(x,y) - h(x-1,y) and
- * sy-(x,y) = h(x,y) - h(x,y-1).  With W = L/64 words per sublattice row, the word at index
- *     ((s * 2 + d) * L + y) * W + j        (s = sublattice, d = 0 for x / 1 for y, row y)
+ * sy-(x,y) = h(x,y) - h(x,y-1).  With W = X/64 words per sublattice row, the word at index
+ *     ((s * 2 + d) * Y + y) * W + j        (s = sublattice, d = 0 for x / 1 for y, row y)
  * holds in bit b the slope of sublattice site k = 32 j + b, lattice site x = 2k + ((s + y) & 1)
  * (the paper's role-grouped "non-local" encoding, Sec. II.A, with this offset convention).
- * Total 4 * L * W words = L*L/4 bytes.
+ * Total 4 * Y * W words = X*Y/4 bytes (L*L/4 for a square lattice).
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11) in place of the paper's TinyMT, keyed by
  * the seed with counter (g, t, s | (draw - 1) << 1 | (t >> 32) << 6, tag | (g >> 32) << 1):
@@ -35,13 +36,13 @@
  *     n draw bits, draw 1 most significant, form R >= 2^n - P (equal to the paper's and/or
  *     construction, xi = r_n; xi = b_i ? r_i | xi : r_i & xi for i = n-1..1);
  *   - any probability (paper Sec. II.B, one random number per site): site unit
- *     u = y * (L/2) + k uses g = u >> 2, lane u & 3, draw 1, tag 1; accepted iff the 32-bit
+ *     u = y * (X/2) + k uses g = u >> 2, lane u & 3, draw 1, tag 1; accepted iff the 32-bit
  *     output < floor(p * 2^32);
  *   - t is the 0-based index of the MCS being executed; deposition and removal share draws.
  *
  * Roughness (paper Sec. I.A names the roughness; its definition here): heights from h(0,0) = 0
  * down column 0 (sy-) then along each row (sx-); S1 = sum h, S2 = sum h^2 (128-bit),
- * num = N * S2 - S1^2 (128-bit), W^2 = num / N^2 with N = L*L.
+ * num = N * S2 - S1^2 (128-bit), W^2 = num / N^2 with N = X*Y.
  */
 #ifndef SCA_H
 #define SCA_H
@@ -74,17 +75,22 @@ extern "C" {
 #define SCA_RNG_UNIFORM32 2  /* one 32-bit uniform per site (Sec. II.B, arbitrary p)       */
 
 typedef struct sca_params {
-    uint32_t L;      /* lateral size: a multiple of 64, 64 <= L <= 131072 */
+    uint32_t L;      /* lateral size X (sites per row): a multiple of 64, 64 <= L <= 131072 */
     uint32_t rng;    /* SCA_RNG_* */
     uint64_t seed;   /* Philox key */
     double p;        /* deposition probability at local minima, 0 <= p <= 1 */
     double q;        /* removal probability at local maxima, 0 <= q <= 1 */
+    uint32_t Ly;     /* lateral size Y (rows): 0 for a square lattice (Y = L), else even,
+                        2 <= Ly <= 131072.  X != Y runs on the two-pass kernel (1) and the
+                        wavefront kernel (4) of sca_set_kernel; batches, servers and
+                        sca_observe_noalloc take square lattices only */
+    uint32_t reserved;  /* 0 */
 } sca_params;
 
 /* One exact roughness observation. */
 typedef struct sca_obs {
     uint64_t t;        /* MCS completed when observed */
-    uint64_t N;        /* L * L */
+    uint64_t N;        /* X * Y sites */
     int64_t S1;        /* sum of heights */
     uint64_t S2_lo;    /* sum of squared heights, low 64 bits */
     uint64_t S2_hi;    /*                        high 64 bits */
@@ -95,6 +101,22 @@ typedef struct sca_obs {
     int32_t reserved;
 } sca_obs;
 
+/* One exact two-time height correlation (see sca_correlate).  Signed 128-bit values are split
+ * into an unsigned low and a signed high 64-bit word. */
+typedef struct sca_corr {
+    uint64_t t;        /* MCS of the simulation's current state (state a) */
+    uint64_t N;        /* X * Y sites */
+    int64_t Sa;        /* sum of the heights of state a (h(0,0) = 0) */
+    int64_t Sb;        /* sum of the heights of the reference state b */
+    uint64_t Sab_lo;   /* sum of h_a h_b over the sites, low 64 bits */
+    int64_t Sab_hi;    /*                                high 64 bits (signed) */
+    uint64_t cnum_lo;  /* N * Sab - Sa * Sb, low 64 bits (C = cnum / N^2) */
+    int64_t cnum_hi;   /*                    high 64 bits (signed) */
+    double c;          /* cnum / N^2 rounded to double */
+    int32_t status;    /* SCA_OK, or SCA_ESTATE if either state does not close */
+    int32_t reserved;
+} sca_corr;
+
 typedef struct sca_sim sca_sim;   /* one simulation: state, stream, scratch; opaque */
 
 /* ---- single lattice ------------------------------------------------------------------------ */
@@ -103,9 +125,13 @@ typedef struct sca_sim sca_sim;   /* one simulation: state, stream, scratch; opa
  * (two state buffers for the ping-pong update, plus observation scratch).  0 if L is invalid. */
 size_t sca_workspace_bytes(uint32_t L);
 
+/* The same for an X x Y lattice (X = sca_params.L, Y = sca_params.Ly); 0 if invalid. */
+size_t sca_workspace_bytes_xy(uint32_t X, uint32_t Y);
+
 /* Create a simulation at MCS 0 in the flat state h(x,y) = (x + y) & 1 (sublattice-0 words all
  * zero, sublattice-1 words all ones).  dev_buf: caller-owned device memory of at least
- * sca_workspace_bytes(L) bytes, 256-byte aligned, or NULL to let the library allocate.
+ * sca_workspace_bytes_xy(L, Ly) bytes (sca_workspace_bytes(L) when square), 256-byte aligned,
+ * or NULL to let the library allocate.
  * Errors: SCA_EINVAL (bad params or short buffer), SCA_ENOMEM, SCA_ECUDA. */
 int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_buf_bytes,
              sca_sim **out);
@@ -126,10 +152,24 @@ int sca_observe(sca_sim *sim, sca_obs *out);
  * Errors: SCA_EINVAL, SCA_ECUDA, SCA_ESTATE (first failing observation's status). */
 int sca_run(sca_sim *sim, const uint64_t *times, uint32_t n, sca_obs *out);
 
-/* Copy the current canonical words to host memory (n_words >= 4 * L * L/64); synchronises. */
+/* Two-time height correlation of the current state a (MCS t) with a reference state b of the
+ * same lattice, typically a copy of an earlier state (MCS s < t): the paper's aging studies
+ * (Sec. I, Sec. IV) measure two-time functions; the one computed here is the covariance of the
+ * two height fields over the sites,
+ *     C(t, s) = (1/N) sum_x (h(x,t) - <h(t)>)(h(x,s) - <h(s)>) = cnum / N^2,
+ * exact in integers (cnum = N sum h_a h_b - sum h_a sum h_b), unchanged by the unknown absolute
+ * height of either state; C(t, t) equals the roughness W^2(t).
+ *   ref_words_dev: caller-owned device memory with the reference state's canonical words
+ *                  (4 * Y * X/64 words, the layout of sca_get_state), read only; e.g. a copy of
+ *                  the words sca_state_device pointed to at MCS s.
+ * Synchronises the stream.  Errors: SCA_EINVAL, SCA_EBUSY (an asynchronous run's records are
+ * still pending), SCA_ECUDA; SCA_ESTATE (in out->status too) if either state does not close. */
+int sca_correlate(sca_sim *sim, const uint32_t *ref_words_dev, sca_corr *out);
+
+/* Copy the current canonical words to host memory (n_words >= 4 * Y * X/64); synchronises. */
 int sca_get_state(sca_sim *sim, uint32_t *host_words, size_t n_words);
 
-/* Replace the state by n_words = 4 * L * L/64 canonical words from host memory and set the
+/* Replace the state by n_words = 4 * Y * X/64 canonical words from host memory and set the
  * MCS count to t (the next step uses MCS index t); synchronises.  The words are accepted as
  * they are; one device pass records whether they form a surface (every plaquette closes and
  * the slopes sum to zero around the torus), which kernel 4 of sca_set_kernel requires, and

@@ -51,8 +51,6 @@ int make_rule(const sca_params &prm, Rule &R)
     std::memset(&R, 0, sizeof(R));
     R.k0 = (uint32_t)prm.seed;
     R.k1 = (uint32_t)(prm.seed >> 32);
-    R.one = 1u;
-    R.two = 2u;
     for (uint32_t r = 0; r < 10; ++r) {          // Philox key schedule, round r
         R.rk[2 * r] = R.k0 + r * 0x9E3779B9u;
         R.rk[2 * r + 1] = R.k1 + r * 0xBB67AE85u;
@@ -82,14 +80,16 @@ int make_rule(const sca_params &prm, Rule &R)
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 
-static bool layout_for(uint32_t L, Layout &lo)
+// X sites per row (a multiple of 64), Y rows (even); both at most 131072.
+static bool layout_for(uint32_t X, uint32_t Y, Layout &lo)
 {
-    if (L < 64 || L % 64 != 0 || L > 131072) return false;
-    const size_t W = L / 64;
-    lo.state_bytes = 4 * (size_t)L * W * sizeof(uint32_t);
+    if (X < 64 || X % 64 != 0 || X > 131072) return false;
+    if (Y < 2 || Y % 2 != 0 || Y > 131072) return false;
+    const size_t W = X / 64;
+    lo.state_bytes = 4 * (size_t)Y * W * sizeof(uint32_t);
     lo.off_b = align256(lo.state_bytes);
     lo.off_h0 = lo.off_b + align256(lo.state_bytes);
-    lo.off_part = lo.off_h0 + align256((size_t)L * sizeof(int64_t));
+    lo.off_part = lo.off_h0 + align256((size_t)Y * sizeof(int64_t));
     lo.off_res = lo.off_part + align256((size_t)(kObsGridCap + 1) * sizeof(ObsPartial));
     lo.off_err = lo.off_res + align256((size_t)kResCap * sizeof(ObsDev));
     lo.total = lo.off_err + 256;
@@ -112,7 +112,13 @@ extern "C" {
 size_t sca_workspace_bytes(uint32_t L)
 {
     Layout lo;
-    return layout_for(L, lo) ? lo.total : 0;
+    return layout_for(L, L, lo) ? lo.total : 0;
+}
+
+size_t sca_workspace_bytes_xy(uint32_t X, uint32_t Y)
+{
+    Layout lo;
+    return layout_for(X, Y, lo) ? lo.total : 0;
 }
 
 int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_buf_bytes,
@@ -121,8 +127,9 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
     if (!params || !out) return fail(SCA_EINVAL, "NULL argument");
     *out = nullptr;
     Layout lo;
-    if (!layout_for(params->L, lo))
-        return fail(SCA_EINVAL, "L must be a multiple of 64 in [64, 131072]");
+    const uint32_t Y = params->Ly ? params->Ly : params->L;
+    if (!layout_for(params->L, Y, lo))
+        return fail(SCA_EINVAL, "L must be a multiple of 64 in [64, 131072] and Ly even in [2, 131072]");
     Rule R;
     int rc = make_rule(*params, R);
     if (rc) return rc;
@@ -134,6 +141,7 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
     s->R = R;
     s->L = params->L;
     s->W = params->L / 64;
+    s->Ly = Y;
     s->lo = lo;
     s->t = 0;
     s->kernel = 0;
@@ -211,6 +219,8 @@ int sca_reset(sca_sim *s)
 int sca_set_kernel(sca_sim *s, int kernel)
 {
     if (!s || kernel < 0 || kernel > 4) return fail(SCA_EINVAL, "kernel must be 0, 1, 2, 3 or 4");
+    if ((kernel == 2 || kernel == 3) && s->Ly != s->L)
+        return fail(SCA_EINVAL, "kernels 2 and 3 take square lattices only");
     if (kernel == 2 && !fused_supported(s->L))
         return fail(SCA_EINVAL, "fused kernel needs L to be a multiple of 2048");
     if (kernel == 3) {
@@ -220,7 +230,7 @@ int sca_set_kernel(sca_sim *s, int kernel)
             return fail(SCA_EINVAL, "temporal blocking does not fit this lattice size");
     }
     if (kernel == 4) {
-        if (!wave_supported(s->L, (uint32_t)wave_max_k((int)s->R.mode), (int)s->R.mode))
+        if (!wave_supported_xy(s->L, s->Ly, (uint32_t)wave_max_k((int)s->R.mode), (int)s->R.mode))
             return fail(SCA_EINVAL, "the wavefront kernel does not fit this lattice size");
     }
     s->kernel = kernel;
@@ -229,8 +239,8 @@ int sca_set_kernel(sca_sim *s, int kernel)
 
 int sca_set_wave_bands(sca_sim *s, int bands)
 {
-    if (!s || bands < 0 || (uint32_t)bands > s->L / 2)
-        return fail(SCA_EINVAL, "bands must be 0 (automatic) or 1..L/2");
+    if (!s || bands < 0 || (uint32_t)bands > s->Ly / 2)
+        return fail(SCA_EINVAL, "bands must be 0 (automatic) or 1..Y/2");
     s->wave_bands = (uint32_t)bands;
     return SCA_OK;
 }
@@ -240,7 +250,7 @@ int sca_set_temporal_block(sca_sim *s, int mcs_per_launch)
     if (!s) return fail(SCA_EINVAL, "NULL simulation");
     const int k = mcs_per_launch > 0 ? mcs_per_launch : 4;
     if (k > 64 || (64 % k) != 0) return fail(SCA_EINVAL, "MCS per launch must divide 64");
-    if (s->kernel == 4) {               // launches of the largest supported power of two <= k
+    if (s->kernel == 4 || s->Ly != s->L) {   // launches of the largest supported power of two <= k
         s->tb_k = k;
         s->tb_set = true;
         return SCA_OK;
@@ -267,23 +277,36 @@ int sca_set_temporal_block(sca_sim *s, int mcs_per_launch)
 // temporal blocking (several MCS per launch) wins while the lattice is small enough that
 // launches and L2 round trips dominate (dyadic draws up to L = 8192, per-site uniforms up to
 // L = 2048); the two-pass kernel covers the rest.
-static uint32_t wave_default_k(uint32_t L, const Rule &R)
+// For an X x Y lattice the thresholds apply to the area (X Y >= L^2), and the MCS per launch
+// are held to at most Y/8 (a band of rows is at least 8 K rows tall, so the recomputed halo
+// stays at most half of what a band streams).
+static bool area_at_least(const sca_sim *s, uint64_t L) { return (uint64_t)s->L * s->Ly >= L * L; }
+
+static uint32_t wave_default_k(const sca_sim *s)
 {
-    if (R.mode == 0) return L >= 16384 ? 16u : 8u;
-    if (R.mode == 2) return 2u;
-    const bool q0 = R.nq == 0 && R.Pq == 0;
-    if (R.n_draws == 1 && q0) return 4u;       // p = 1/2: the lightest draws, the deepest window
-    return R.n_draws >= 3 && !q0 ? 1u : 2u;
+    const Rule &R = s->R;
+    uint32_t k;
+    if (R.mode == 0) {
+        k = area_at_least(s, 16384) ? 16u : 8u;
+    } else if (R.mode == 2) {
+        k = 2u;
+    } else {
+        const bool q0 = R.nq == 0 && R.Pq == 0;
+        if (R.n_draws == 1 && q0) k = 4u;       // p = 1/2: the lightest draws, the deepest window
+        else k = R.n_draws >= 3 && !q0 ? 1u : 2u;
+    }
+    while (k > 1 && 8u * k > s->Ly) k /= 2;
+    return k;
 }
 
 static bool wave_auto(const sca_sim *s)
 {
     if (!s->surface) return false;
     const Rule &R = s->R;
-    if (R.mode == 0) return s->L >= 4096;
+    if (R.mode == 0) return area_at_least(s, 4096);
     if (R.mode != 1 || s->L % 256 != 0) return false;
-    if (R.n_draws <= 2) return s->L >= 32768;
-    return R.n_draws == 3 && s->L >= 65536;
+    if (R.n_draws <= 2) return area_at_least(s, 32768);
+    return R.n_draws == 3 && area_at_least(s, 65536);
 }
 
 // An asynchronous state load decides `surface` when its check completes; the first decision
@@ -293,7 +316,7 @@ static int resolve_surface(sca_sim *s)
     if (!s->chk_pending) return SCA_OK;
     cudaError_t e = cudaEventSynchronize(s->chk_ev);
     if (e != cudaSuccess) return cuda_fail(e, "surface check");
-    s->surface = surface_from(s->chk_host, s->L);
+    s->surface = surface_from(s->chk_host, s->L, s->Ly);
     s->chk_pending = false;
     return SCA_OK;
 }
@@ -303,14 +326,17 @@ int sca::effective_kernel(const sca_sim *s, int *tb_k)
     int k = s->kernel;
     int kk = s->tb_k;
     const int mode = (int)s->R.mode;
-    if (k == 4) kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : wave_default_k(s->L, s->R), mode);
+    const bool square = s->Ly == s->L;
+    if (k == 4) kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : wave_default_k(s), mode);
     if (k == 0) {
         uint32_t ns;
         size_t sm;
-        const bool wave_ok = wave_auto(s) && wave_supported(s->L, wave_default_k(s->L, s->R), mode);
+        const bool wave_ok = wave_auto(s) && wave_supported_xy(s->L, s->Ly, wave_default_k(s), mode);
         if (wave_ok) {
             k = 4;
-            kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : wave_default_k(s->L, s->R), mode);
+            kk = (int)wave_pick_k(s->tb_set ? (uint32_t)kk : wave_default_k(s), mode);
+        } else if (!square) {                   // X != Y: the two-pass kernel covers the rest
+            k = 1;
         } else if (fused_supported(s->L) && s->L >= 32768 && s->R.mode != 2) {
             k = 2;
         } else if (s->R.mode != 2 && s->L <= 8192 && tblock_plan(s->L, s->tb_set ? kk : 8, &ns, &sm)) {
@@ -389,8 +415,8 @@ int sca::step_impl(sca_sim *s, uint64_t n)
             cudaError_t e = kern == 3
                 ? launch_tblock(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->t + done, (uint32_t)k,
                                 s->R, s->stream)
-                : launch_wave(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->t + done, (uint32_t)kk,
-                              s->R, s->stream, nullptr, s->wave_bands);
+                : launch_wave_xy(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->Ly, s->t + done, (uint32_t)kk,
+                                 s->R, s->stream, nullptr, s->wave_bands);
             if (e != cudaSuccess) {
                 s->t += done;
                 return cuda_fail(e, "temporal-blocking launch");
@@ -419,8 +445,8 @@ int sca::step_impl(sca_sim *s, uint64_t n)
                                  s->stream, nullptr, s->fused_V, s->fused_ring);
             if (e == cudaSuccess) s->cur ^= 1;
         } else {
-            e = launch_half_step(s->buf[s->cur], s->L, t, 0, s->R, s->stream);
-            if (e == cudaSuccess) e = launch_half_step(s->buf[s->cur], s->L, t, 1, s->R, s->stream);
+            e = launch_half_step_xy(s->buf[s->cur], s->L, s->Ly, t, 0, s->R, s->stream);
+            if (e == cudaSuccess) e = launch_half_step_xy(s->buf[s->cur], s->L, s->Ly, t, 1, s->R, s->stream);
         }
         if (e != cudaSuccess) {
             s->t = t;
@@ -466,8 +492,8 @@ int sca_run(sca_sim *s, const uint64_t *times, uint32_t n, sca_obs *out)
         for (uint32_t i = 0; i < chunk; ++i) {
             int rc = step_impl(s, times[done + i] - s->t);
             if (rc) return rc;
-            cudaError_t e = launch_observe(s->buf[s->cur], s->L, s->h0, s->part, s->res + i, s->t,
-                                           s->stream);
+            cudaError_t e = launch_observe_xy(s->buf[s->cur], s->L, s->Ly, s->part, s->res + i, s->t,
+                                              s->stream);
             if (e != cudaSuccess) return cuda_fail(e, "observe launch");
         }
         uint32_t err = 0;
@@ -498,6 +524,24 @@ int sca_observe(sca_sim *s, sca_obs *out)
     return sca_run(s, &t, 1, out);
 }
 
+int sca_correlate(sca_sim *s, const uint32_t *ref_words_dev, sca_corr *out)
+{
+    if (!s || !ref_words_dev || !out) return fail(SCA_EINVAL, "NULL argument");
+    if (s->async_obs) return fail(SCA_EBUSY, "collect the asynchronous run's records first (sca_wait)");
+    static_assert(sizeof(sca_corr) <= kResCap * sizeof(ObsDev), "the record fits the result area");
+    if (corr_record_bytes() != sizeof(sca_corr)) return fail(SCA_ECUDA, "correlation record layout");
+    cudaError_t e = launch_correlate(s->buf[s->cur], ref_words_dev, s->L, s->Ly, s->part, s->res, s->t,
+                                     s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, s->res, sizeof(sca_corr), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sca_correlate");
+    const double cn = std::ldexp((double)out->cnum_hi, 64) + (double)out->cnum_lo;
+    const double N = (double)out->N;
+    out->c = cn / (N * N);
+    if (out->status) return fail(out->status, "slopes do not close around the torus");
+    return SCA_OK;
+}
+
 int sca_get_state(sca_sim *s, uint32_t *host_words, size_t n_words)
 {
     if (!s || !host_words) return fail(SCA_EINVAL, "NULL argument");
@@ -517,7 +561,7 @@ int sca_set_state(sca_sim *s, const uint32_t *host_words, size_t n_words, uint64
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sca_set_state");
     bool surf = false;
-    e = surface_check(s->buf[s->cur], s->L, reinterpret_cast<uint32_t *>(s->part), s->stream, &surf);
+    e = surface_check(s->buf[s->cur], s->L, s->Ly, reinterpret_cast<uint32_t *>(s->part), s->stream, &surf);
     if (e != cudaSuccess) return cuda_fail(e, "surface check");
     s->surface = surf;
     s->chk_pending = false;
@@ -537,7 +581,7 @@ int sca_set_state_async(sca_sim *s, const uint32_t *host_words, size_t n_words, 
     cudaError_t e = cudaMemcpyAsync(s->buf[s->cur], host_words, s->lo.state_bytes,
                                     cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
-        e = surface_check_async(s->buf[s->cur], s->L, reinterpret_cast<uint32_t *>(s->part), s->chk_host,
+        e = surface_check_async(s->buf[s->cur], s->L, s->Ly, reinterpret_cast<uint32_t *>(s->part), s->chk_host,
                                 s->stream);
     if (e == cudaSuccess) e = cudaEventRecord(s->chk_ev, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sca_set_state_async");
@@ -568,7 +612,7 @@ int sca_run_async(sca_sim *s, const uint64_t *times, uint32_t n)
     for (uint32_t i = 0; i < n; ++i) {
         int rc = step_impl(s, times[i] - s->t);
         if (rc) return rc;
-        cudaError_t e = launch_observe(s->buf[s->cur], s->L, s->h0, s->part, s->res + i, s->t, s->stream);
+        cudaError_t e = launch_observe_xy(s->buf[s->cur], s->L, s->Ly, s->part, s->res + i, s->t, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "observe launch");
     }
     s->async_obs = n;

@@ -1201,6 +1201,10 @@ int sca_batch_init(const sca_params *params, uint32_t count, void *stream, sca_b
             delete b;
             return fail(SCA_EINVAL, "batch lattices need L a multiple of 64 in [128, 2048]");
         }
+        if (params[i].Ly != 0 && params[i].Ly != L) {
+            delete b;
+            return fail(SCA_EINVAL, "batch lattices are square (Ly = 0 or L)");
+        }
         BatchLattice &lt = b->lat[i];
         std::memset(&lt, 0, sizeof(lt));
         int rc = make_rule(params[i], lt.R);
@@ -1541,7 +1545,7 @@ int sca_batch_set_state(sca_batch *b, uint32_t index, const uint32_t *host_words
     bool surface = false;
     cudaError_t e = cudaMemcpyAsync(dst, host_words, need * sizeof(uint32_t), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&scratch, 4 * sizeof(uint32_t), b->stream);
-    if (e == cudaSuccess) e = surface_check(dst, L, scratch, b->stream, &surface);
+    if (e == cudaSuccess) e = surface_check(dst, L, L, scratch, b->stream, &surface);
     if (scratch) {
         const cudaError_t e2 = cudaFreeAsync(scratch, b->stream);
         if (e == cudaSuccess) e = e2;

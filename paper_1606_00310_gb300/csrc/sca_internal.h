@@ -42,6 +42,9 @@ struct ObsPartial {
 // steps be replayed; launch_add_t / launch_set_t maintain the counter).
 cudaError_t launch_half_step(uint32_t *A, uint32_t L, uint64_t t, int s, const Rule &R,
                              cudaStream_t st, const uint64_t *t_dev = nullptr);
+// The same on an X x Y lattice (X sites per row, Y rows); launch_half_step is X = Y = L.
+cudaError_t launch_half_step_xy(uint32_t *A, uint32_t X, uint32_t Y, uint64_t t, int s, const Rule &R,
+                                cudaStream_t st, const uint64_t *t_dev = nullptr);
 cudaError_t launch_add_t(uint64_t *t_dev, uint64_t n, cudaStream_t st);
 cudaError_t launch_set_t(uint64_t *t_dev, uint64_t v, cudaStream_t st);
 // err: device word; bit 0 is set if a pipeline wait gave up (the result is then invalid).
@@ -61,18 +64,23 @@ bool tblock_plan(uint32_t L, uint32_t k, uint32_t *nslabs, size_t *smem);
 cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t0, uint32_t k,
                         const Rule &R, cudaStream_t st, const uint64_t *t_dev = nullptr,
                         uint32_t bands = 0);
+// The same on an X x Y lattice (X sites per row, Y rows).
+cudaError_t launch_wave_xy(const uint32_t *src, uint32_t *dst, uint32_t X, uint32_t Y, uint64_t t0, uint32_t k,
+                           const Rule &R, cudaStream_t st, const uint64_t *t_dev = nullptr,
+                           uint32_t bands = 0);
 bool wave_supported(uint32_t L, uint32_t k, int mode);
+bool wave_supported_xy(uint32_t X, uint32_t Y, uint32_t k, int mode);
 int wave_max_k(int mode);
 uint32_t wave_pick_k(uint32_t want, int mode);   // largest supported power of two <= want
 // Is A a surface (every plaquette closes, row 0 and column 0 close around the torus)?  Uses 3
 // words of device scratch; synchronises the stream.
-cudaError_t surface_check(const uint32_t *A, uint32_t L, uint32_t *scratch, cudaStream_t st,
+cudaError_t surface_check(const uint32_t *A, uint32_t X, uint32_t Y, uint32_t *scratch, cudaStream_t st,
                           bool *is_surface);
 // The same check enqueued only: the three result words land in host3 (pinned) when the stream
-// gets there; surface_from() reads them.
-cudaError_t surface_check_async(const uint32_t *A, uint32_t L, uint32_t *scratch, uint32_t *host3,
+// gets there; surface_from() reads them.  X sites per row, Y rows.
+cudaError_t surface_check_async(const uint32_t *A, uint32_t X, uint32_t Y, uint32_t *scratch, uint32_t *host3,
                                 cudaStream_t st);
-bool surface_from(const uint32_t *host3, uint32_t L);
+bool surface_from(const uint32_t *host3, uint32_t X, uint32_t Y);
 bool fused_shape_ok(uint32_t L, int V, int ring);
 size_t fused_smem_bytes(uint32_t L);
 
@@ -100,9 +108,18 @@ size_t obs_batch_scratch_bytes(uint32_t n_lat, uint32_t L);
 // Observation kernels: h0 scratch of L int64; partials scratch of obs_partials(L) + 1 entries
 // (never more than kObsGridCap + 1).
 constexpr int kObsGridCap = 2048;
-int obs_partials(uint32_t L);
+int obs_partials(uint32_t rows);
 cudaError_t launch_observe(const uint32_t *A, uint32_t L, int64_t *h0, ObsPartial *partials,
                            ObsDev *result, uint64_t t, cudaStream_t st);
+// The same on an X x Y lattice (X sites per row, Y rows; N = X * Y).
+cudaError_t launch_observe_xy(const uint32_t *A, uint32_t X, uint32_t Y, ObsPartial *partials, ObsDev *result,
+                              uint64_t t, cudaStream_t st);
+
+// Two-time height correlation of the states A and B of one X x Y lattice (chunk records in
+// partials, at most obs_partials scratch; result record of corr_record_bytes() bytes).
+cudaError_t launch_correlate(const uint32_t *A, const uint32_t *B, uint32_t X, uint32_t Y, ObsPartial *partials,
+                             void *result, uint64_t t, cudaStream_t st);
+size_t corr_record_bytes();
 
 void count_launches(uint64_t n);
 int sm_count();
@@ -120,7 +137,8 @@ struct sca_params;
 // One single-lattice simulation (opaque on the ABI).
 struct sca_sim {
     sca::Rule R;
-    uint32_t L, W;
+    uint32_t L, W;      // row length X (sites) and words per sublattice row
+    uint32_t Ly;        // rows Y (L for a square lattice)
     sca::Layout lo;
     char *base;
     bool own_mem;

@@ -106,7 +106,8 @@ static_assert(sizeof(ObsChunk) == 2 * sizeof(ObsPartial), "chunk records fill tw
 // walks words [l W / 32, (l+1) W / 32) of the row's even-x plane (sublattice y & 1) and odd-x
 // plane (sublattice (y & 1) ^ 1), i.e. x in [64 j, 64 j + 64) for each owned word j.
 template <bool VEC>
-__device__ void obs_rows_chunk(const uint32_t *A, uint32_t L, uint32_t r0, uint32_t r1, ObsChunk *chunk)
+__device__ void obs_rows_chunk(const uint32_t *A, uint32_t L, uint32_t Y, uint32_t r0, uint32_t r1,
+                               ObsChunk *chunk)
 {
     __shared__ uint32_t tabr[256 * 32];
     __shared__ int64_t sA[kObsChunkRows];
@@ -121,8 +122,8 @@ __device__ void obs_rows_chunk(const uint32_t *A, uint32_t L, uint32_t r0, uint3
     if (threadIdx.x < kObsChunkRows / 32) sbits[threadIdx.x] = 0;
     if (threadIdx.x == 0) red_flag = 0;
     __syncthreads();
-    const uint32_t W = L / 64;
-    const size_t plane = (size_t)L * W;
+    const uint32_t W = L / 64;                  // L: sites per row; Y: rows
+    const size_t plane = (size_t)Y * W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t *tab = tabr + lane;
     const uint32_t c0 = (uint32_t)(((uint64_t)lane * W) / 32), c1 = (uint32_t)(((uint64_t)(lane + 1) * W) / 32);
@@ -218,14 +219,14 @@ __device__ void obs_rows_chunk(const uint32_t *A, uint32_t L, uint32_t r0, uint3
     }
 }
 
-// Block b owns the contiguous rows [b L / G, (b+1) L / G) of the lattice.
+// Block b owns the contiguous rows [b Y / G, (b+1) Y / G) of the lattice (L sites per row).
 template <bool VEC>
-__global__ void __launch_bounds__(32 * kObsRowsWarps) k_obs_rows(const uint32_t *A, uint32_t L,
+__global__ void __launch_bounds__(32 * kObsRowsWarps) k_obs_rows(const uint32_t *A, uint32_t L, uint32_t Y,
                                                                 ObsChunk *chunks)
 {
-    const uint32_t r0 = (uint32_t)(((uint64_t)blockIdx.x * L) / gridDim.x);
-    const uint32_t r1 = (uint32_t)(((uint64_t)(blockIdx.x + 1) * L) / gridDim.x);
-    obs_rows_chunk<VEC>(A, L, r0, r1, chunks + blockIdx.x);
+    const uint32_t r0 = (uint32_t)(((uint64_t)blockIdx.x * Y) / gridDim.x);
+    const uint32_t r1 = (uint32_t)(((uint64_t)(blockIdx.x + 1) * Y) / gridDim.x);
+    obs_rows_chunk<VEC>(A, L, Y, r0, r1, chunks + blockIdx.x);
 }
 
 // Many lattices of one size: block b takes chunk b % nch of lattice b / nch (first word at
@@ -235,14 +236,15 @@ __global__ void __launch_bounds__(32 * kObsRowsWarps) k_obs_rows_batch(const uin
 {
     const uint32_t li = blockIdx.x / nch, c = blockIdx.x - li * nch;
     const uint32_t r0 = (uint32_t)(((uint64_t)c * L) / nch), r1 = (uint32_t)(((uint64_t)(c + 1) * L) / nch);
-    obs_rows_chunk<false>(base + off[li], L, r0, r1, chunks + blockIdx.x);
+    obs_rows_chunk<false>(base + off[li], L, L, r0, r1, chunks + blockIdx.x);
 }
 
 // One block: thread c takes chunk c, P_c = sum of U over earlier chunks (block scan), then
+// with L sites per row and Y rows (N = L Y)
 //   S1 = sum_c L (n_c P_c + Sh_c) + SA_c,
 //   S2 = sum_c L (n_c P_c^2 + 2 P_c Sh_c + Sh2_c) + 2 (P_c SA_c + ShA_c) + SB_c,
 // num = N S2 - S1^2, all in 128-bit integers.  Flags: bit 0 column 0 does not close around y
-// (h(0, L-1) + s(0) != 0), bit 1 some row does not close around x.
+// (h(0, Y-1) + s(0) != 0), bit 1 some row does not close around x.
 constexpr int kObsFinalThreads = 1024;
 
 __device__ __forceinline__ void block_sum_i128(__int128 &v, __int128 *sh)
@@ -267,7 +269,7 @@ __device__ __forceinline__ void block_sum_i128(__int128 &v, __int128 *sh)
 }
 
 __global__ void __launch_bounds__(kObsFinalThreads) k_obs_final(const ObsChunk *chunks, int nchunks,
-                                                                uint32_t L, uint64_t t, ObsDev *out)
+                                                                uint32_t L, uint32_t Y, uint64_t t, ObsDev *out)
 {
     __shared__ __int128 sh[32];
     __shared__ int64_t wsum[32];
@@ -297,12 +299,12 @@ __global__ void __launch_bounds__(kObsFinalThreads) k_obs_final(const ObsChunk *
     block_sum_i128(s2, sh);
     if (tid != 0) return;
     flags = fl;
-    // closure around the y cycle: h(0, L-1) + s(0) must return to h(0, 0) = 0
+    // closure around the y cycle: h(0, Y-1) + s(0) must return to h(0, 0) = 0
     const int64_t s0 = (flags & 4u) ? 1 : -1;
     flags &= 3u;
     if (col_total + s0 != 0) flags |= 1u;
     const unsigned __int128 S2 = (unsigned __int128)s2;
-    const unsigned __int128 N = (unsigned __int128)L * L;
+    const unsigned __int128 N = (unsigned __int128)L * Y;
     const unsigned __int128 num = N * S2 - (unsigned __int128)(s1 * s1);
     out->t = t;
     out->N = (uint64_t)N;
@@ -366,6 +368,231 @@ __global__ void k_obs_final_batch(const ObsChunk *chunks, uint32_t nch, uint32_t
     out[(size_t)dst[li] * stride] = o;
 }
 
+// ---------------------------------------------------------------------- two-time correlation
+// C(t, s) for two states A (the simulation's) and B (a reference) of one X x Y lattice:
+// Sa = sum h_a, Sb = sum h_b, Sab = sum h_a h_b, cnum = N Sab - Sa Sb, each height from
+// h(0, 0) = 0 as in the roughness.  Per row y, with g = h - h(0, y): A_a = sum_x g_a,
+// A_b = sum_x g_b, AB = sum_x g_a g_b, and sum_x h_a h_b = X ha0 hb0 + ha0 A_b + hb0 A_a + AB
+// (ha0 = h_a(0, y)).  Column 0 is integrated per chunk as in the roughness (ha0 = P_a + hl_a).
+struct CorrChunk {
+    int64_t Ua, Ub;            // column-0 slope totals over the chunk's rows y >= 1
+    int64_t Sha, Shb, Shab;    // sums of hl_a, hl_b, hl_a hl_b
+    int64_t Aa, Ab;            // sums of A_a, A_b
+    int64_t ShaAb, ShbAa;      // sums of hl_a A_b, hl_b A_a
+    int64_t AB;                // sum of AB
+    uint32_t n, flags;         // rows; bit 1 a row does not close, bit 2 / 3: s_a(0) / s_b(0) = +1
+    int64_t pad[5];
+};
+static_assert(sizeof(CorrChunk) == 4 * sizeof(ObsPartial), "a correlation chunk fills four partial slots");
+constexpr int kCorrChunkCap = kObsGridCap / 4;
+
+// One warp per row of the chunk [r0, r1); lane l walks words [l W / 32, (l+1) W / 32) of the
+// row's even-x and odd-x planes of both states, site by site in x order.
+__global__ void __launch_bounds__(32 * kObsRowsWarps) k_corr_rows(const uint32_t *A, const uint32_t *B, uint32_t X,
+                                                                 uint32_t Y, CorrChunk *chunks)
+{
+    __shared__ int64_t sAa[kObsChunkRows], sAb[kObsChunkRows], sAB[kObsChunkRows];
+    __shared__ uint32_t bits_a[kObsChunkRows / 32], bits_b[kObsChunkRows / 32];
+    __shared__ uint32_t red_flag;
+    const uint32_t r0 = (uint32_t)(((uint64_t)blockIdx.x * Y) / gridDim.x);
+    const uint32_t r1 = (uint32_t)(((uint64_t)(blockIdx.x + 1) * Y) / gridDim.x);
+    if (threadIdx.x < kObsChunkRows / 32) bits_a[threadIdx.x] = bits_b[threadIdx.x] = 0;
+    if (threadIdx.x == 0) red_flag = 0;
+    __syncthreads();
+    const uint32_t W = X / 64;
+    const size_t plane = (size_t)Y * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t c0 = (uint32_t)(((uint64_t)lane * W) / 32), c1 = (uint32_t)(((uint64_t)(lane + 1) * W) / 32);
+    const int64_t n = 64 * (int64_t)(c1 - c0);
+    for (uint32_t y = r0 + warp; y < r1; y += kObsRowsWarps) {
+        const uint32_t se = y & 1u, so = se ^ 1u;
+        const size_t oe = (size_t)(se * 2) * plane + (size_t)y * W, oo = (size_t)(so * 2) * plane + (size_t)y * W;
+        int32_t da = 0, db = 0;
+        int64_t sda = 0, sdb = 0, sdab = 0;
+        for (uint32_t j = c0; j < c1; ++j) {
+            const uint32_t ea = A[oe + j], oa = A[oo + j], eb = B[oe + j], ob = B[oo + j];
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                da += 2 * (int32_t)((ea >> k) & 1u) - 1;
+                db += 2 * (int32_t)((eb >> k) & 1u) - 1;
+                sda += da;
+                sdb += db;
+                sdab += (int64_t)da * db;
+                da += 2 * (int32_t)((oa >> k) & 1u) - 1;
+                db += 2 * (int32_t)((ob >> k) & 1u) - 1;
+                sda += da;
+                sdb += db;
+                sdab += (int64_t)da * db;
+            }
+        }
+        // place the lanes' pieces (E: offset before the lane's first site, from x = 0 inclusive;
+        // g(x) = offset(x) - s(0), the slope of site 0 not being part of h(0, y))
+        const int64_t ia = warp_incl_scan((int64_t)da), ib = warp_incl_scan((int64_t)db);
+        const int64_t ta = __shfl_sync(0xFFFFFFFFu, ia, 31), tb = __shfl_sync(0xFFFFFFFFu, ib, 31);
+        uint32_t w0a = 0, w0b = 0, ca = 0, cb = 0;
+        if (lane == 0) {
+            w0a = A[oe];
+            w0b = B[oe];
+            ca = A[(size_t)(se * 2 + 1) * plane + (size_t)y * W] & 1u;
+            cb = B[(size_t)(se * 2 + 1) * plane + (size_t)y * W] & 1u;
+        }
+        w0a = __shfl_sync(0xFFFFFFFFu, w0a, 0);
+        w0b = __shfl_sync(0xFFFFFFFFu, w0b, 0);
+        const int64_t Ga = (ia - da) - (2 * (int64_t)(w0a & 1u) - 1);
+        const int64_t Gb = (ib - db) - (2 * (int64_t)(w0b & 1u) - 1);
+        const int64_t Aa = warp_sum(n * Ga + sda);
+        const int64_t Ab = warp_sum(n * Gb + sdb);
+        const int64_t AB = warp_sum(n * Ga * Gb + Ga * sdb + Gb * sda + sdab);
+        if (lane == 0) {
+            sAa[y - r0] = Aa;
+            sAb[y - r0] = Ab;
+            sAB[y - r0] = AB;
+            if (ca) atomicOr(&bits_a[(y - r0) >> 5], 1u << ((y - r0) & 31));
+            if (cb) atomicOr(&bits_b[(y - r0) >> 5], 1u << ((y - r0) & 31));
+            if (ta != 0 || tb != 0) atomicOr(&red_flag, 2u);
+        }
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    const uint32_t m = r1 - r0;
+    const uint32_t a0 = (uint32_t)(((uint64_t)lane * m) / 32), a1 = (uint32_t)(((uint64_t)(lane + 1) * m) / 32);
+    auto slope = [&](const uint32_t *bits, uint32_t i) -> int64_t {
+        if (r0 + i == 0) return 0;
+        return 2 * (int64_t)((bits[i >> 5] >> (i & 31)) & 1u) - 1;
+    };
+    int64_t ua = 0, ub = 0;
+    for (uint32_t i = a0; i < a1; ++i) {
+        ua += slope(bits_a, i);
+        ub += slope(bits_b, i);
+    }
+    const int64_t uia = warp_incl_scan(ua), uib = warp_incl_scan(ub);
+    int64_t hla = uia - ua, hlb = uib - ub;
+    int64_t Sha = 0, Shb = 0, Shab = 0, SAa = 0, SAb = 0, ShaAb = 0, ShbAa = 0, SAB = 0;
+    for (uint32_t i = a0; i < a1; ++i) {
+        hla += slope(bits_a, i);
+        hlb += slope(bits_b, i);
+        Sha += hla;
+        Shb += hlb;
+        Shab += hla * hlb;
+        SAa += sAa[i];
+        SAb += sAb[i];
+        ShaAb += hla * sAb[i];
+        ShbAa += hlb * sAa[i];
+        SAB += sAB[i];
+    }
+    CorrChunk ch{};
+    ch.Ua = __shfl_sync(0xFFFFFFFFu, uia, 31);
+    ch.Ub = __shfl_sync(0xFFFFFFFFu, uib, 31);
+    ch.Sha = warp_sum(Sha);
+    ch.Shb = warp_sum(Shb);
+    ch.Shab = warp_sum(Shab);
+    ch.Aa = warp_sum(SAa);
+    ch.Ab = warp_sum(SAb);
+    ch.ShaAb = warp_sum(ShaAb);
+    ch.ShbAa = warp_sum(ShbAa);
+    ch.AB = warp_sum(SAB);
+    if (lane == 0) {
+        ch.n = m;
+        ch.flags = red_flag | ((r0 == 0 && (bits_a[0] & 1u)) ? 4u : 0u) | ((r0 == 0 && (bits_b[0] & 1u)) ? 8u : 0u);
+        chunks[blockIdx.x] = ch;
+    }
+}
+
+// Result of one correlation (the layout of sca_corr).
+struct CorrDev {
+    uint64_t t, N;
+    int64_t Sa, Sb;
+    uint64_t Sab_lo;
+    int64_t Sab_hi;
+    uint64_t cnum_lo;
+    int64_t cnum_hi;
+    double c;
+    int32_t status, reserved;
+};
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *wsum, int64_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t incl = warp_incl_scan(v);
+    __syncthreads();
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t u = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        wsum[lane] = warp_incl_scan(u);
+    }
+    __syncthreads();
+    *total = wsum[(blockDim.x >> 5) - 1];
+    return incl - v + (warp > 0 ? wsum[warp - 1] : 0);
+}
+
+__global__ void __launch_bounds__(kCorrChunkCap) k_corr_final(const CorrChunk *chunks, int nchunks, uint32_t X,
+                                                             uint32_t Y, uint64_t t, CorrDev *out)
+{
+    __shared__ __int128 sh[32];
+    __shared__ int64_t wsum[32];
+    __shared__ uint32_t fl;
+    const int tid = threadIdx.x, lane = tid & 31;
+    CorrChunk ch{};
+    if (tid < nchunks) ch = chunks[tid];
+    if (tid == 0) fl = 0;
+    int64_t tot_a = 0, tot_b = 0;
+    const int64_t Pa = block_excl_scan(ch.Ua, wsum, &tot_a);
+    const int64_t Pb = block_excl_scan(ch.Ub, wsum, &tot_b);
+    const __int128 Xi = (__int128)X, ni = (__int128)ch.n, pa = (__int128)Pa, pb = (__int128)Pb;
+    __int128 sa = Xi * (ni * pa + ch.Sha) + ch.Aa;
+    __int128 sb = Xi * (ni * pb + ch.Shb) + ch.Ab;
+    __int128 sab = Xi * (ni * pa * pb + pa * ch.Shb + pb * ch.Sha + ch.Shab) + pa * ch.Ab + ch.ShaAb +
+                   pb * ch.Aa + ch.ShbAa + ch.AB;
+    uint32_t flags = __reduce_or_sync(0xFFFFFFFFu, ch.flags);
+    if (lane == 0 && flags) atomicOr(&fl, flags);
+    block_sum_i128(sa, sh);
+    block_sum_i128(sb, sh);
+    block_sum_i128(sab, sh);
+    if (tid != 0) return;
+    flags = fl;
+    uint32_t bad = flags & 2u;
+    if (tot_a + ((flags & 4u) ? 1 : -1) != 0) bad |= 1u;    // column 0 of A closes around y
+    if (tot_b + ((flags & 8u) ? 1 : -1) != 0) bad |= 1u;    // column 0 of B closes around y
+    const __int128 N = (__int128)X * Y;
+    const __int128 cnum = N * sab - sa * sb;
+    out->t = t;
+    out->N = (uint64_t)N;
+    out->Sa = (int64_t)sa;
+    out->Sb = (int64_t)sb;
+    out->Sab_lo = (uint64_t)sab;
+    out->Sab_hi = (int64_t)(sab >> 64);
+    out->cnum_lo = (uint64_t)cnum;
+    out->cnum_hi = (int64_t)(cnum >> 64);
+    out->c = 0.0;
+    out->status = bad ? -7 : 0;     // SCA_ESTATE
+    out->reserved = (int32_t)bad;
+}
+
+size_t corr_record_bytes() { return sizeof(CorrDev); }
+
+// chunks of at most kObsChunkRows rows, at most kCorrChunkCap of them, about 4 per SM
+static int corr_chunks(uint32_t rows)
+{
+    int g = sm_count() * 4;
+    if (g > kCorrChunkCap) g = kCorrChunkCap;
+    if ((uint32_t)g > rows) g = (int)rows;
+    while ((rows + g - 1) / g > (uint32_t)kObsChunkRows) g *= 2;
+    return g;
+}
+
+cudaError_t launch_correlate(const uint32_t *A, const uint32_t *B, uint32_t X, uint32_t Y, ObsPartial *partials,
+                             void *result, uint64_t t, cudaStream_t st)
+{
+    const int grid = corr_chunks(Y);
+    if (grid > kCorrChunkCap) return cudaErrorInvalidValue;
+    CorrChunk *chunks = reinterpret_cast<CorrChunk *>(partials);
+    k_corr_rows<<<grid, 32 * kObsRowsWarps, 0, st>>>(A, B, X, Y, chunks);
+    k_corr_final<<<1, kCorrChunkCap, 0, st>>>(chunks, grid, X, Y, t, static_cast<CorrDev *>(result));
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 // Chunks per lattice for the batched observation (rows per chunk at most kObsChunkRows,
 // at most 32 chunks).
 uint32_t obs_batch_chunks(uint32_t L)
@@ -393,13 +620,13 @@ size_t obs_batch_scratch_bytes(uint32_t n_lat, uint32_t L)
     return (size_t)n_lat * obs_batch_chunks(L) * sizeof(ObsChunk);
 }
 
-int obs_partials(uint32_t L)
+int obs_partials(uint32_t rows)
 {
     // chunks of at most kObsChunkRows rows, at most kObsChunkCap of them, about 4 per SM
     int g = sm_count() * 4;
     if (g > kObsChunkCap) g = kObsChunkCap;
-    if ((uint32_t)g > L) g = (int)L;
-    while ((L + g - 1) / g > (uint32_t)kObsChunkRows) g *= 2;
+    if ((uint32_t)g > rows) g = (int)rows;
+    while ((rows + g - 1) / g > (uint32_t)kObsChunkRows) g *= 2;
     return g;
 }
 
@@ -408,13 +635,19 @@ cudaError_t launch_observe(const uint32_t *A, uint32_t L, int64_t *h0, ObsPartia
                            ObsDev *result, uint64_t t, cudaStream_t st)
 {
     (void)h0;
-    const uint32_t W = L / 64;
-    const int grid = obs_partials(L);
+    return launch_observe_xy(A, L, L, partials, result, t, st);
+}
+
+cudaError_t launch_observe_xy(const uint32_t *A, uint32_t X, uint32_t Y, ObsPartial *partials, ObsDev *result,
+                              uint64_t t, cudaStream_t st)
+{
+    const uint32_t W = X / 64;
+    const int grid = obs_partials(Y);
     if (grid > kObsChunkCap) return cudaErrorInvalidValue;
     ObsChunk *chunks = reinterpret_cast<ObsChunk *>(partials);
-    if (W % 128 == 0) k_obs_rows<true><<<grid, 32 * kObsRowsWarps, 0, st>>>(A, L, chunks);
-    else k_obs_rows<false><<<grid, 32 * kObsRowsWarps, 0, st>>>(A, L, chunks);
-    k_obs_final<<<1, kObsFinalThreads, 0, st>>>(chunks, grid, L, t, result);
+    if (W % 128 == 0) k_obs_rows<true><<<grid, 32 * kObsRowsWarps, 0, st>>>(A, X, Y, chunks);
+    else k_obs_rows<false><<<grid, 32 * kObsRowsWarps, 0, st>>>(A, X, Y, chunks);
+    k_obs_final<<<1, kObsFinalThreads, 0, st>>>(chunks, grid, X, Y, t, result);
     count_launches(2);
     return cudaGetLastError();
 }

@@ -40,7 +40,8 @@ __device__ __forceinline__ void st_words(uint32_t *p, const uint32_t (&r)[V])
 
 struct HalfArgs {
     uint32_t *A;
-    uint32_t L, W;
+    uint32_t L, W;       // row length X (sites) and its words per sublattice row
+    uint32_t Y;          // rows
     uint64_t t;          // MCS index, or its offset from *t_dev when t_dev is set
     const uint64_t *t_dev;
     int s;
@@ -61,20 +62,20 @@ __global__ void __launch_bounds__(512) k_half_step(const HalfArgs a)
     uint32_t *sh_first = sh + team * a.TP;              // first sx+ source word of each lane
     uint32_t *sh_carry = sh + tpb * a.TP + team * a.TP; // top mask bit of each lane
     const int s = a.s, ns = s ^ 1;
-    const uint32_t L = a.L, W = a.W;
+    const uint32_t L = a.L, W = a.W, Y = a.Y;
     const uint64_t t = a.t_dev ? *a.t_dev + a.t : a.t;
-    const size_t plane = (size_t)L * W;
+    const size_t plane = (size_t)Y * W;
     uint32_t *Asx = a.A + (size_t)(s * 2 + 0) * plane;
     uint32_t *Asy = a.A + (size_t)(s * 2 + 1) * plane;
     uint32_t *Anx = a.A + (size_t)(ns * 2 + 0) * plane;
     uint32_t *Any = a.A + (size_t)(ns * 2 + 1) * plane;
 
-    for (uint32_t base = blockIdx.x * tpb; base < L; base += gridDim.x * tpb) {
+    for (uint32_t base = blockIdx.x * tpb; base < Y; base += gridDim.x * tpb) {
         const uint32_t y = base + team;
-        const bool active = owner && y < L;
+        const bool active = owner && y < Y;
         const uint32_t j = (uint32_t)lane * V;
         const size_t row = (size_t)y * W + j;
-        const size_t rown = (size_t)(y + 1 == L ? 0 : y + 1) * W + j;
+        const size_t rown = (size_t)(y + 1 == Y ? 0 : y + 1) * W + j;
         const bool shifted = ((s + y) & 1u) != 0;
 
         uint32_t xm[V], ym[V], nx[V], ny[V];
@@ -183,7 +184,7 @@ template <int V, int MODE>
 static cudaError_t launch_half_v(const HalfArgs &a, const TeamShape &ts, cudaStream_t st)
 {
     const int rows_per_block = ts.teams;
-    int grid = (int)((a.L + rows_per_block - 1) / rows_per_block);
+    int grid = (int)((a.Y + rows_per_block - 1) / rows_per_block);
     const int cap = sm_count() * (2048 / ts.block);
     if (grid > cap) grid = cap;
     const size_t smem = 2 * sizeof(uint32_t) * ts.block;
@@ -195,9 +196,15 @@ static cudaError_t launch_half_v(const HalfArgs &a, const TeamShape &ts, cudaStr
 cudaError_t launch_half_step(uint32_t *A, uint32_t L, uint64_t t, int s, const Rule &R,
                              cudaStream_t st, const uint64_t *t_dev)
 {
-    const uint32_t W = L / 64;
+    return launch_half_step_xy(A, L, L, t, s, R, st, t_dev);
+}
+
+cudaError_t launch_half_step_xy(uint32_t *A, uint32_t X, uint32_t Y, uint64_t t, int s, const Rule &R,
+                                cudaStream_t st, const uint64_t *t_dev)
+{
+    const uint32_t W = X / 64;
     const TeamShape ts = team_shape(W, 256);
-    HalfArgs a{A, L, W, t, t_dev, s, ts.T, ts.TP, R};
+    HalfArgs a{A, X, W, Y, t, t_dev, s, ts.T, ts.TP, R};
     const int mode = (int)R.mode;
 #define SCA_HALF(VV)                                                        \
     if (ts.V == VV) {                                                       \

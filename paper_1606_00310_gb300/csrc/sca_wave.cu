@@ -84,43 +84,52 @@ static int blocks_for(int K, int V, const Rule &R)
 }
 
 // Bands of rows: enough tiles (warps) for one full wave of resident warps, but bands of at
-// least 8K rows so the recomputed halo stays at most half of the streamed rows.
-static bool wave_plan(uint32_t L, uint32_t k, int mode, uint32_t bands, int blocks_per_sm,
+// least 8K rows so the recomputed halo stays at most half of the streamed rows.  X sites per
+// row (the tiles' columns of words), Y rows (the bands).
+static bool wave_plan(uint32_t X, uint32_t Y, uint32_t k, int mode, uint32_t bands, int blocks_per_sm,
                       uint32_t *nbands, uint32_t *ncols)
 {
-    if (L < 64 || L % 64 != 0 || k == 0 || (k & (k - 1)) != 0) return false;
+    if (X < 64 || X % 64 != 0 || Y < 2 || Y % 2 != 0 || k == 0 || (k & (k - 1)) != 0) return false;
     if ((int)k > wave_max_k(mode)) return false;
-    const uint32_t W = L / 64, tw = kWaveTileWords * (uint32_t)wave_V(L, mode, k);
+    const uint32_t W = X / 64, tw = kWaveTileWords * (uint32_t)wave_V(X, mode, k);
     const uint32_t nc = (W + tw - 1) / tw;
     uint32_t nb = bands;
     if (nb == 0) {
         const uint64_t warps = (uint64_t)sm_count() * blocks_per_sm * kWaveWarps;
         nb = (uint32_t)(warps / nc);            // every tile resident at once: no tail wave
-        const uint32_t cap = L / (8u * k);
+        const uint32_t cap = Y / (8u * k);
         if (nb > cap) nb = cap;
         if (nb == 0) nb = 1;
     }
-    if (nb > L / 2) return false;
+    if (nb > Y / 2) return false;
     *nbands = nb;
     *ncols = nc;
     return true;
 }
 
-bool wave_supported(uint32_t L, uint32_t k, int mode)
+bool wave_supported(uint32_t L, uint32_t k, int mode) { return wave_supported_xy(L, L, k, mode); }
+
+bool wave_supported_xy(uint32_t X, uint32_t Y, uint32_t k, int mode)
 {
     uint32_t nb, nc;
-    return wave_plan(L, wave_pick_k(k, mode), mode, 0, 1, &nb, &nc);
+    return wave_plan(X, Y, wave_pick_k(k, mode), mode, 0, 1, &nb, &nc);
 }
 
 cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t0, uint32_t k,
                         const Rule &R, cudaStream_t st, const uint64_t *t_dev, uint32_t bands)
 {
+    return launch_wave_xy(src, dst, L, L, t0, k, R, st, t_dev, bands);
+}
+
+cudaError_t launch_wave_xy(const uint32_t *src, uint32_t *dst, uint32_t X, uint32_t Y, uint64_t t0, uint32_t k,
+                           const Rule &R, cudaStream_t st, const uint64_t *t_dev, uint32_t bands)
+{
     const int mode = (int)R.mode;
     uint32_t nb, nc;
-    if (!wave_plan(L, k, mode, bands, 1, &nb, &nc)) return cudaErrorInvalidValue;
-    const int V = wave_V(L, mode, k);
-    if (!wave_plan(L, k, mode, bands, blocks_for((int)k, V, R), &nb, &nc)) return cudaErrorInvalidValue;
-    const WaveArgs a{src, dst, L, L / 64, nb, nc, t0, t_dev, R};
+    if (!wave_plan(X, Y, k, mode, bands, 1, &nb, &nc)) return cudaErrorInvalidValue;
+    const int V = wave_V(X, mode, k);
+    if (!wave_plan(X, Y, k, mode, bands, blocks_for((int)k, V, R), &nb, &nc)) return cudaErrorInvalidValue;
+    const WaveArgs a{src, dst, X, X / 64, Y, nb, nc, t0, t_dev, R};
     const uint64_t tiles = (uint64_t)nb * nc;
     const int grid = (int)((tiles + kWaveWarps - 1) / kWaveWarps);
     count_launches(1);
@@ -140,16 +149,17 @@ cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t
 // A state is a surface when every plaquette closes and the slopes sum to zero around the torus
 // along row 0 and column 0 (then along every row and column).  For the plaquette with corners
 // (x-1, y-1) and (x, y): sx-(x, y) - sx-(x, y-1) == sy-(x, y) - sy-(x-1, y), i.e. with slope
-// bits a, b, c, d: a + d == b + c.  One thread per canonical word of sublattice s, row y.
-__global__ void k_surface_check(const uint32_t *A, uint32_t L, uint32_t W, uint32_t *out)
+// bits a, b, c, d: a + d == b + c.  One thread per canonical word of sublattice s, row y; Y rows
+// of W words per sublattice.
+__global__ void k_surface_check(const uint32_t *A, uint32_t Y, uint32_t W, uint32_t *out)
 {
-    const size_t plane = (size_t)L * W;
+    const size_t plane = (size_t)Y * W;
     const size_t n = 2 * plane;
     for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += (size_t)gridDim.x * blockDim.x) {
         const uint32_t s = (uint32_t)(w / plane);
         const size_t rem = w - (size_t)s * plane;
         const uint32_t y = (uint32_t)(rem / W), j = (uint32_t)(rem - (size_t)y * W);
-        const uint32_t ns = s ^ 1u, yp = y == 0 ? L - 1 : y - 1, jp = j == 0 ? W - 1 : j - 1;
+        const uint32_t ns = s ^ 1u, yp = y == 0 ? Y - 1 : y - 1, jp = j == 0 ? W - 1 : j - 1;
         const uint32_t *SXs = A + (size_t)(2 * s) * plane, *SYs = A + (size_t)(2 * s + 1) * plane;
         const uint32_t *SXn = A + (size_t)(2 * ns) * plane, *SYn = A + (size_t)(2 * ns + 1) * plane;
         const uint32_t a = SXs[(size_t)y * W + j];
@@ -166,34 +176,35 @@ __global__ void k_surface_check(const uint32_t *A, uint32_t L, uint32_t W, uint3
     }
 }
 
-bool surface_from(const uint32_t *h, uint32_t L) { return h[0] == 0 && h[1] == L / 2 && h[2] == L / 2; }
+// Row 0 holds X/2 sx- ones and column 0 Y/2 sy- ones when both close.
+bool surface_from(const uint32_t *h, uint32_t X, uint32_t Y) { return h[0] == 0 && h[1] == X / 2 && h[2] == Y / 2; }
 
-cudaError_t surface_check_async(const uint32_t *A, uint32_t L, uint32_t *scratch, uint32_t *host3,
+cudaError_t surface_check_async(const uint32_t *A, uint32_t X, uint32_t Y, uint32_t *scratch, uint32_t *host3,
                                 cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    const uint32_t W = L / 64;
-    const size_t n = 2 * (size_t)L * W;
+    const uint32_t W = X / 64;
+    const size_t n = 2 * (size_t)Y * W;
     int grid = (int)((n + 255) / 256);
     if (grid > sm_count() * 8) grid = sm_count() * 8;
-    k_surface_check<<<grid, 256, 0, st>>>(A, L, W, scratch);
+    k_surface_check<<<grid, 256, 0, st>>>(A, Y, W, scratch);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(host3, scratch, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
 }
 
-cudaError_t surface_check(const uint32_t *A, uint32_t L, uint32_t *scratch, cudaStream_t st,
+cudaError_t surface_check(const uint32_t *A, uint32_t X, uint32_t Y, uint32_t *scratch, cudaStream_t st,
                           bool *is_surface)
 {
     cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    const uint32_t W = L / 64;
-    const size_t n = 2 * (size_t)L * W;
+    const uint32_t W = X / 64;
+    const size_t n = 2 * (size_t)Y * W;
     int grid = (int)((n + 255) / 256);
     if (grid > sm_count() * 8) grid = sm_count() * 8;
-    k_surface_check<<<grid, 256, 0, st>>>(A, L, W, scratch);
+    k_surface_check<<<grid, 256, 0, st>>>(A, Y, W, scratch);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -201,7 +212,7 @@ cudaError_t surface_check(const uint32_t *A, uint32_t L, uint32_t *scratch, cuda
     e = cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
-    *is_surface = surface_from(h, L);
+    *is_surface = surface_from(h, X, Y);
     return cudaSuccess;
 }
 

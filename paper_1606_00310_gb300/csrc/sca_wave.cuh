@@ -36,7 +36,8 @@ namespace sca {
 struct WaveArgs {
     const uint32_t *src;
     uint32_t *dst;
-    uint32_t L, W;
+    uint32_t L, W;           // sites per row (X) and words per sublattice row
+    uint32_t Y;              // rows
     uint32_t nbands, ncols;  // tiles: bands of rows x columns of words
     uint64_t t0;             // MCS index of the first step, or offset from *t_dev
     const uint64_t *t_dev;
@@ -253,8 +254,8 @@ __device__ __forceinline__ uint32_t wave_update(uint32_t b, uint32_t up, uint32_
 // R - i (slot S + 1 + u - i).  yu is the lattice row of row R (used by the random draws).
 template <int K, int V, int U, int MODE, bool DP, bool DQ, int ND>
 __device__ __forceinline__ void wave_half_steps(const Rule &Rl, uint32_t (&h)[2 * K + 1 + U][2][V], const int u,
-                                                const uint32_t yu, const uint32_t L, const uint32_t W,
-                                                const uint32_t j, const uint64_t t0)
+                                                const uint32_t yu, const uint32_t L, const uint32_t Y,
+                                                const uint32_t W, const uint32_t j, const uint64_t t0)
 {
     constexpr int S = 2 * K;
     constexpr int base = S + 1;
@@ -287,14 +288,14 @@ __device__ __forceinline__ void wave_half_steps(const Rule &Rl, uint32_t (&h)[2 
         uint32_t xp[V] = {}, xq[V] = {};
         if constexpr (MODE == 2) {
             // one 32-bit uniform per site (Sec. II.B), four sites per Philox call
-            const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
+            const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + Y - (uint32_t)i;
 #pragma unroll
             for (int v = 0; v < V; ++v)
                 xi_uniform_word(Rl, Rl.rk, (uint64_t)y * (L / 2) + 32u * (j + v), t0 + (uint32_t)((i - 1) >> 1), s,
                                 0u, xp[v], xq[v]);
         }
         if constexpr (MODE == 1) {
-            const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
+            const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + Y - (uint32_t)i;
             const KeysRk key{Rl.rk};
             if constexpr (ND == 0)
                 wave_xi<V>(Rl, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
@@ -395,7 +396,7 @@ __device__ __forceinline__ void wave_block01(const Rule &Rl, WaveTile &T, uint32
         }
         T.ol += T.W;
         if (T.ol >= T.plane) T.ol -= T.plane;
-        wave_half_steps<K, V, U, 0, DP, DQ, 0>(Rl, h, u, 0u, T.L, T.W, T.j, 0u);
+        wave_half_steps<K, V, U, 0, DP, DQ, 0>(Rl, h, u, 0u, T.L, T.L, T.W, T.j, 0u);
         if (!CHK || R >= 4u * K + 2u) {         // row R - 2K is final
             wave_store_row<V>(h[base + u - S], h[base + u - S - 1], u, T.own, T.os, T.DX0, T.DY0, T.DX1, T.DY1);
             T.os += T.W;
@@ -419,16 +420,17 @@ __global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) 
     const uint32_t tile = blockIdx.x * kWaveWarps + threadIdx.x / 32;
     if (tile >= a.nbands * a.ncols) return;
     const uint32_t band = tile / a.ncols, col = tile - band * a.ncols;
-    const uint32_t L = a.L, W = a.W;
+    const uint32_t L = a.L, W = a.W, Y = a.Y;   // L sites per row, Y rows
     // band rows [y0, y1), y0 even: the first streamed row is even, so band-row parity is
     // lattice-row parity
-    const uint32_t y0 = 2u * (uint32_t)(((uint64_t)band * (L / 2)) / a.nbands);
-    const uint32_t y1 = 2u * (uint32_t)(((uint64_t)(band + 1) * (L / 2)) / a.nbands);
+    const uint32_t y0 = 2u * (uint32_t)(((uint64_t)band * (Y / 2)) / a.nbands);
+    const uint32_t y1 = 2u * (uint32_t)(((uint64_t)(band + 1) * (Y / 2)) / a.nbands);
     // halo: 2K rows below, 2K + 2 above (the top row's sy- words need the row above it, and
-    // the first streamed row stays even)
+    // the first streamed row stays even); rows are taken modulo Y, so a band taller than the
+    // lattice streams some rows twice, as the periodic lattice unrolled along y
     const uint32_t NR = y1 - y0 + 4u * K + 2u;
-    const uint32_t first = (y0 + 2u * L - 2u * K - 2u) % L;
-    const size_t plane = (size_t)L * W;
+    const uint32_t first = (uint32_t)(((uint64_t)y0 + 64ull * Y - 2u * K - 2u) % Y);
+    const size_t plane = (size_t)Y * W;
     const uint32_t *SX0 = a.src, *SY0 = a.src + plane, *SX1 = a.src + 2 * plane, *SY1 = a.src + 3 * plane;
     uint32_t *DX0 = a.dst, *DY0 = a.dst + plane, *DX1 = a.dst + 2 * plane, *DY1 = a.dst + 3 * plane;
     const uint64_t t0 = a.t_dev ? *a.t_dev + a.t0 : a.t0;
@@ -481,8 +483,8 @@ __global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) 
             h[S + 1][1][v] = pre[v] ^ flip ^ nsx1[v];
         }
     }
-    const uint32_t plane32 = L * W;
-    uint32_t ol = (first + 1 >= L ? first + 1 - L : first + 1) * W + j;     // next row to load
+    const uint32_t plane32 = Y * W;
+    uint32_t ol = (first + 1 >= Y ? first + 1 - Y : first + 1) * W + j;     // next row to load
 #pragma unroll
     for (int u = 1; u < P; ++u) {
         if ((uint32_t)u < NR) {
@@ -522,12 +524,12 @@ __global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) 
                 }
                 ol += W;
                 if (ol >= plane32) ol -= plane32;
-                wave_half_steps<K, V, U, MODE, DP, DQ, ND>(a.R, h, u, yu, L, W, j, t0);
+                wave_half_steps<K, V, U, MODE, DP, DQ, ND>(a.R, h, u, yu, L, Y, W, j, t0);
                 if (R >= 4u * K + 2u) {         // row R - 2K is final
                     wave_store_row<V>(h[base + u - S], h[base + u - S - 1], u, own, os, DX0, DY0, DX1, DY1);
                     os += W;
                 }
-                if (++yu == L) yu = 0;
+                if (++yu == Y) yu = 0;
             }
             wave_slide<K, V, U>(h);
         }

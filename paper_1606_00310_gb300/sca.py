@@ -21,7 +21,7 @@ KERNEL_AUTO, KERNEL_TWO_PASS, KERNEL_FUSED, KERNEL_TBLOCK, KERNEL_WAVE = 0, 1, 2
 
 class sca_params(C.Structure):
     _fields_ = [("L", C.c_uint32), ("rng", C.c_uint32), ("seed", C.c_uint64),
-                ("p", C.c_double), ("q", C.c_double)]
+                ("p", C.c_double), ("q", C.c_double), ("Ly", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class sca_obs(C.Structure):
@@ -29,6 +29,13 @@ class sca_obs(C.Structure):
                 ("S2_lo", C.c_uint64), ("S2_hi", C.c_uint64),
                 ("num_lo", C.c_uint64), ("num_hi", C.c_uint64),
                 ("w2", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
+class sca_corr(C.Structure):
+    _fields_ = [("t", C.c_uint64), ("N", C.c_uint64), ("Sa", C.c_int64), ("Sb", C.c_int64),
+                ("Sab_lo", C.c_uint64), ("Sab_hi", C.c_int64), ("cnum_lo", C.c_uint64),
+                ("cnum_hi", C.c_int64), ("c", C.c_double), ("status", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class sca_request_info(C.Structure):
@@ -47,6 +54,7 @@ class sca_server_stats(C.Structure):
 # Every symbol include/sca.h declares, with its ctypes signature.
 SIGNATURES = {
     "sca_workspace_bytes": (C.c_size_t, [C.c_uint32]),
+    "sca_workspace_bytes_xy": (C.c_size_t, [C.c_uint32, C.c_uint32]),
     "sca_init": (C.c_int, [C.POINTER(sca_params), C.c_void_p, C.c_void_p, C.c_size_t,
                            C.POINTER(C.c_void_p)]),
     "sca_reset": (C.c_int, [C.c_void_p]),
@@ -54,6 +62,7 @@ SIGNATURES = {
     "sca_observe": (C.c_int, [C.c_void_p, C.POINTER(sca_obs)]),
     "sca_run": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.c_uint32, C.POINTER(sca_obs)]),
     "sca_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "sca_correlate": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(sca_corr)]),
     "sca_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint64]),
     "sca_state_device": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "sca_time": (C.c_uint64, [C.c_void_p]),
@@ -140,8 +149,11 @@ def check(code, where):
         raise ScaError(code, where)
 
 
-def workspace_bytes(L: int) -> int:
-    return int(load().sca_workspace_bytes(L))
+def workspace_bytes(L: int, Ly: int = None) -> int:
+    """Device bytes of one simulation of L x L sites, or of L sites per row and Ly rows."""
+    if Ly is None:
+        return int(load().sca_workspace_bytes(L))
+    return int(load().sca_workspace_bytes_xy(L, Ly))
 
 
 def measure_logic_rate() -> float:
@@ -181,6 +193,24 @@ class Obs:
                    status=int(o.status))
 
 
+@dataclass
+class Corr:
+    """Two-time height correlation: C = cnum / N^2 (cnum = N Sab - Sa Sb, exact)."""
+    t: int
+    N: int
+    Sa: int
+    Sb: int
+    Sab: int
+    cnum: int
+    c: float
+    status: int
+
+    @staticmethod
+    def from_c(o: sca_corr) -> "Corr":
+        return Corr(o.t, o.N, o.Sa, o.Sb, (o.Sab_hi << 64) | o.Sab_lo, (o.cnum_hi << 64) | o.cnum_lo,
+                    o.c, o.status)
+
+
 def observe_noalloc(words_dev_ptr: int, L: int, t: int = 0, stream=None) -> Obs:
     """Exact roughness of caller-owned device words without any library allocation (the
     scratch is a fixed device array shared by all calls; serialise overlapping calls)."""
@@ -192,25 +222,28 @@ def observe_noalloc(words_dev_ptr: int, L: int, t: int = 0, stream=None) -> Obs:
     return Obs.from_c(o)
 
 
-def words_count(L: int) -> int:
-    return 4 * L * (L // 64)
+def words_count(L: int, Ly: int = None) -> int:
+    """Canonical words of an L x L lattice, or of L sites per row and Ly rows."""
+    return 4 * (L if Ly is None else Ly) * (L // 64)
 
 
 class Sim:
-    """One L x L lattice on the current CUDA device, flat at MCS 0.
+    """One L x L lattice on the current CUDA device, flat at MCS 0; with Ly, a lattice of L
+    sites per row and Ly rows.
 
-    ``workspace`` may be a caller-owned uint8 CUDA tensor of at least workspace_bytes(L);
+    ``workspace`` may be a caller-owned uint8 CUDA tensor of at least workspace_bytes(L, Ly);
     otherwise one is allocated with PyTorch.  ``stream`` is a torch.cuda.Stream (default: a new
     stream of the current device); all of the simulation's kernels run on it."""
 
     def __init__(self, L, seed=1, p=1.0, q=0.0, rng=RNG_AUTO, stream=None, workspace=None,
-                 kernel=KERNEL_AUTO):
+                 kernel=KERNEL_AUTO, Ly=None):
         import torch
         lib = load()
         self.L = int(L)
-        nbytes = workspace_bytes(self.L)
+        self.Ly = self.L if Ly is None else int(Ly)
+        nbytes = workspace_bytes(self.L, self.Ly)
         if nbytes == 0:
-            raise ScaError(EINVAL, "L=%d" % L)
+            raise ScaError(EINVAL, "L=%d Ly=%d" % (self.L, self.Ly))
         if workspace is None:
             workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         if workspace.numel() * workspace.element_size() < nbytes or not workspace.is_cuda:
@@ -220,12 +253,13 @@ class Sim:
             stream = torch.cuda.Stream()
             stream.wait_stream(torch.cuda.current_stream())   # workspace allocation order
         self.stream = stream
-        prm = sca_params(L=self.L, rng=rng, seed=seed, p=p, q=q)
+        prm = sca_params(L=self.L, rng=rng, seed=seed, p=p, q=q,
+                         Ly=0 if self.Ly == self.L else self.Ly)
         h = C.c_void_p()
         check(lib.sca_init(C.byref(prm), C.c_void_p(self.stream.cuda_stream),
                            C.c_void_p(workspace.data_ptr()), nbytes, C.byref(h)), "sca_init")
         self._h = h
-        self.params = dict(L=self.L, seed=seed, p=p, q=q, rng=rng)
+        self.params = dict(L=self.L, Ly=self.Ly, seed=seed, p=p, q=q, rng=rng)
         if kernel != KERNEL_AUTO:
             self.set_kernel(kernel)
 
@@ -274,6 +308,25 @@ class Sim:
             check(rc, "sca_run")
         return [Obs.from_c(o) for o in out]
 
+    def snapshot(self):
+        """A device copy (int32 CUDA tensor) of the current canonical words, the reference state
+        of a later correlate()."""
+        return self.state_tensor().clone()
+
+    def correlate(self, ref) -> "Corr":
+        """Two-time height correlation of the current state with ``ref``, a CUDA tensor holding
+        canonical words of this lattice (e.g. from snapshot())."""
+        import torch
+        n = words_count(self.L, self.Ly)
+        if not ref.is_cuda or ref.numel() * ref.element_size() != 4 * n or not ref.is_contiguous():
+            raise ValueError("ref must be a contiguous CUDA tensor of %d words" % n)
+        self.stream.wait_stream(torch.cuda.current_stream())
+        o = sca_corr()
+        rc = load().sca_correlate(self._h, C.c_void_p(ref.data_ptr()), C.byref(o))
+        if rc not in (OK, ESTATE):
+            check(rc, "sca_correlate")
+        return Corr.from_c(o)
+
     # -- kernel timing (CUDA events around update launches on this simulation's stream)
     def timing(self, enable: bool):
         check(load().sca_timing(self._h, 1 if enable else 0), "sca_timing")
@@ -286,7 +339,7 @@ class Sim:
 
     # -- state
     def get_state(self, out: np.ndarray = None) -> np.ndarray:
-        n = words_count(self.L)
+        n = words_count(self.L, self.Ly)
         if out is None:
             out = np.empty(n, dtype=np.uint32)
         assert out.dtype == np.uint32 and out.size >= n and out.flags.c_contiguous
@@ -338,7 +391,7 @@ class Sim:
         p = C.c_void_p()
         check(load().sca_state_device(self._h, C.byref(p)), "sca_state_device")
         off = p.value - self.workspace.data_ptr()
-        n = words_count(self.L)
+        n = words_count(self.L, self.Ly)
         torch.cuda.current_stream().wait_stream(self.stream)
         return self.workspace[off:off + 4 * n].view(torch.int32)
 
