@@ -74,6 +74,10 @@ def lib():
         L.oracle_pack_rect.restype = None
         L.oracle_unpack_rect.argtypes = [C.c_int64, C.c_int64, u32p, u8p, u8p]
         L.oracle_unpack_rect.restype = None
+        L.oracle_run_rect_counted.argtypes = [C.c_int64, C.c_int64, u8p, u8p, C.c_uint64, C.c_double,
+                                              C.c_double, C.c_int, C.c_uint64, C.c_uint64,
+                                              C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.oracle_run_rect_counted.restype = C.c_int
         L.oracle_corr_rect.argtypes = [C.c_int64, C.c_int64, u8p, u8p, u8p, u8p,
                                        C.POINTER(C.c_int64), C.POINTER(C.c_int64), i64p, i64p]
         L.oracle_corr_rect.restype = C.c_int
@@ -283,3 +287,17 @@ def corr(a, b):
         return (int(v[1]) << 64) + (int(v[0]) & 0xFFFFFFFFFFFFFFFF)
     return {"Sa": int(Sa.value), "Sb": int(Sb.value), "Sab": i128(Sab), "cnum": i128(cn),
             "N": X * Y}
+
+
+def run_rect_counted(bx, by, seed, p, q, mode=None, t0=0, n_mcs=1):
+    """As run_rect; returns (origin_dh, total_dh): the summed height changes (+2 per deposition,
+    -2 per removal) of site (0, 0) and of all sites over these MCS."""
+    Y, X = bx.shape
+    if mode is None:
+        mode = rng_mode(p, q)
+    org = C.c_int64(0)
+    tot = C.c_int64(0)
+    if lib().oracle_run_rect_counted(X, Y, bx, by, seed, float(p), float(q), mode, t0, n_mcs,
+                                     C.byref(org), C.byref(tot)) != 0:
+        raise ValueError("oracle_run_rect_counted: bad parameters")
+    return int(org.value), int(tot.value)

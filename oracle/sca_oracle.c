@@ -185,9 +185,9 @@ static int accepted(const rule_t *r, uint64_t t, int s, int64_t x, int64_t y, in
 
 /* One attempted update of site (x,y) per Eq. (1); bx/by hold sx- / sy- bits row-major with X
  * sites per row.  Rows are addressed through `row` so that the band variant below can reuse
- * the rule. */
-static void update_site(const rule_t *r, uint8_t *bx, uint8_t *by, int64_t X,
-                        int64_t row, int64_t row_next, int64_t x, int64_t y, uint64_t t, int s)
+ * the rule.  Returns the site's height change: +2 (deposition), -2 (removal) or 0. */
+static int update_site(const rule_t *r, uint8_t *bx, uint8_t *by, int64_t X,
+                       int64_t row, int64_t row_next, int64_t x, int64_t y, uint64_t t, int s)
 {
     int64_t xr = (x + 1) % X;
     uint8_t *a = &bx[row * X + x];        /* sx-(x,y)            */
@@ -198,7 +198,9 @@ static void update_site(const rule_t *r, uint8_t *bx, uint8_t *by, int64_t X,
     int is_max = (*a == 1 && *b == 1 && *c == 0 && *d == 0);
     if ((is_min && accepted(r, t, s, x, y, 0)) || (is_max && accepted(r, t, s, x, y, 1))) {
         *a ^= 1; *b ^= 1; *c ^= 1; *d ^= 1;
+        return is_min ? 2 : -2;
     }
+    return 0;
 }
 
 /* Flat initial surface h(x,y) = (x + y) & 1: sx-(x,y) = h(x,y) - h(x-1,y) is -1 on even
@@ -216,23 +218,40 @@ void oracle_init_flat_rect(int64_t X, int64_t Y, uint8_t *bx, uint8_t *by)
 void oracle_init_flat(int64_t L, uint8_t *bx, uint8_t *by) { oracle_init_flat_rect(L, L, bx, by); }
 
 /* Run n_mcs Monte-Carlo steps starting at MCS index t0 (Sec. I.A schedule) on the X x Y
- * lattice.  Returns 0, or -1 on bad parameters. */
-int oracle_run_rect(int64_t X, int64_t Y, uint8_t *bx, uint8_t *by, uint64_t seed, double p,
-                    double q, int mode, uint64_t t0, uint64_t n_mcs)
+ * lattice, adding to *origin_dh the height changes of site (0, 0) (+2 per deposition, -2 per
+ * removal there: with the absolute height of the origin known at the start, it stays known,
+ * and with it the absolute mean height, whose rate of change is the growth velocity) and to
+ * *total_dh those of every site (either pointer may be NULL).  Returns 0, or -1 on bad
+ * parameters. */
+int oracle_run_rect_counted(int64_t X, int64_t Y, uint8_t *bx, uint8_t *by, uint64_t seed, double p,
+                            double q, int mode, uint64_t t0, uint64_t n_mcs, int64_t *origin_dh,
+                            int64_t *total_dh)
 {
     rule_t r;
     if (X < 2 || (X & 1) || Y < 2 || (Y & 1)) return -1;
     if (rule_make(&r, X, seed, p, q, mode)) return -1;
+    int64_t org = 0, tot = 0;
     for (uint64_t t = t0; t < t0 + n_mcs; t++) {
         for (int s = 0; s <= 1; s++) {
-            #pragma omp parallel for schedule(static)
+            #pragma omp parallel for schedule(static) reduction(+:org, tot)
             for (int64_t y = 0; y < Y; y++)
                 for (int64_t x = 0; x < X; x++)
-                    if (((x + y) & 1) == s)
-                        update_site(&r, bx, by, X, y, (y + 1) % Y, x, y, t, s);
+                    if (((x + y) & 1) == s) {
+                        int dh = update_site(&r, bx, by, X, y, (y + 1) % Y, x, y, t, s);
+                        tot += dh;
+                        if (x == 0 && y == 0) org += dh;
+                    }
         }
     }
+    if (origin_dh) *origin_dh += org;
+    if (total_dh) *total_dh += tot;
     return 0;
+}
+
+int oracle_run_rect(int64_t X, int64_t Y, uint8_t *bx, uint8_t *by, uint64_t seed, double p,
+                    double q, int mode, uint64_t t0, uint64_t n_mcs)
+{
+    return oracle_run_rect_counted(X, Y, bx, by, seed, p, q, mode, t0, n_mcs, NULL, NULL);
 }
 
 int oracle_run(int64_t L, uint8_t *bx, uint8_t *by, uint64_t seed, double p, double q,

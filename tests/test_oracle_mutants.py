@@ -5,7 +5,8 @@ neighbour index, a dropped condition, swapped sublattice order, an off-by-one or
 order in the dyadic construction, a wrong Philox operand, a non-strict threshold, a wrong height
 path, a wrong packed offset, a missing flip, a missing counter field, q replaced by p, and on X x Y
 lattices a row count and a row length confused with each other, a wrong factor or sign in the
-two-time correlation) and runs
+two-time correlation, the origin's height change counted at a neighbour or with the wrong sign)
+and runs
 the oracle pin tests against the mutant.  CPU only; the GPU library is not involved.
 """
 import os
@@ -21,10 +22,10 @@ MUTANTS = {
     "sx_plus_left": ("int64_t xr = (x + 1) % X;", "int64_t xr = (x + X - 1) % X;"),
     "drop_c_in_min": ("int is_min = (*a == 0 && *b == 0 && *c == 1 && *d == 1);",
                       "int is_min = (*a == 0 && *b == 0 && *d == 1);"),
-    "odd_first": ("for (int s = 0; s <= 1; s++) {\n            #pragma omp parallel for schedule(static)\n"
+    "odd_first": ("for (int s = 0; s <= 1; s++) {\n            #pragma omp parallel for schedule(static) reduction(+:org, tot)\n"
                   "            for (int64_t y = 0; y < Y; y++)",
                   "for (int s1 = 0; s1 <= 1; s1++) { int s = 1 - s1;\n"
-                  "            #pragma omp parallel for schedule(static)\n"
+                  "            #pragma omp parallel for schedule(static) reduction(+:org, tot)\n"
                   "            for (int64_t y = 0; y < Y; y++)"),
     "dyadic_off_by_one": ("return R >= ((uint64_t)1 << n) - P;", "return R > ((uint64_t)1 << n) - P;"),
     "dyadic_lsb_first": ("for (int i = 1; i <= n; i++) R = (R << 1) | draw_bits[i - 1];",
@@ -43,8 +44,8 @@ MUTANTS = {
     "removal_uses_p": ("uint64_t P = removal ? r->Pq : r->Pp;", "uint64_t P = r->Pp;"),
     "t_missing_from_counter": ("ctr[1] = (uint32_t)t;", "ctr[1] = 0;"),
     # X x Y lattices: a row count or row length used where the other belongs
-    "rect_row_successor_mod_X": ("update_site(&r, bx, by, X, y, (y + 1) % Y, x, y, t, s);",
-                                 "update_site(&r, bx, by, X, y, (y + 1) % X, x, y, t, s);"),
+    "rect_row_successor_mod_X": ("int dh = update_site(&r, bx, by, X, y, (y + 1) % Y, x, y, t, s);",
+                                 "int dh = update_site(&r, bx, by, X, y, (y + 1) % X, x, y, t, s);"),
     "rect_pack_plane_of_X_rows": ("uint64_t idx = ((uint64_t)(s * 2 + d) * (uint64_t)Y + (uint64_t)y) * W + (k >> 5);",
                                   "uint64_t idx = ((uint64_t)(s * 2 + d) * (uint64_t)X + (uint64_t)y) * W + (k >> 5);"),
     "rect_N_is_X_squared": ("unsigned __int128 N = (unsigned __int128)((uint64_t)X * (uint64_t)Y);",
@@ -52,6 +53,9 @@ MUTANTS = {
     "rect_draws_keyed_by_row_count": (
         "if (X < 2 || (X & 1) || Y < 2 || (Y & 1)) return -1;\n    if (rule_make(&r, X, seed, p, q, mode))",
         "if (X < 2 || (X & 1) || Y < 2 || (Y & 1)) return -1;\n    if (rule_make(&r, Y, seed, p, q, mode))"),
+    # origin height counter
+    "origin_counts_a_neighbour": ("if (x == 0 && y == 0) org += dh;", "if (x == 1 && y == 0) org += dh;"),
+    "height_change_sign_of_removal": ("return is_min ? 2 : -2;", "return 2;"),
     # two-time correlation
     "corr_product_uses_a_twice": ("Sab += (__int128)ha[i] * hb[i];", "Sab += (__int128)ha[i] * ha[i];"),
     "corr_numerator_sign": ("__int128 cnum = (__int128)n * Sab - Sa * Sb;",
@@ -67,6 +71,8 @@ PIN_TESTS = ["tests/test_oracle_philox.py", "tests/test_oracle_decisions.py",
 RECT_PINS = ["tests/test_oracle_rect.py"]
 CORR_ONLY = {"corr_product_uses_a_twice", "corr_numerator_sign"}
 CORR_PINS = ["tests/test_oracle_corr.py"]
+HEIGHT_ONLY = {"origin_counts_a_neighbour", "height_change_sign_of_removal"}
+HEIGHT_PINS = ["tests/test_oracle_height.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -80,7 +86,8 @@ def test_mutant_is_caught(name, tmp_path):
     shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests",
                     ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutants.py"))
     shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
-    pins = RECT_PINS if name in RECT_ONLY else CORR_PINS if name in CORR_ONLY else PIN_TESTS
+    pins = (RECT_PINS if name in RECT_ONLY else CORR_PINS if name in CORR_ONLY else
+            HEIGHT_PINS if name in HEIGHT_ONLY else PIN_TESTS)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         *pins], cwd=str(tmp_path), capture_output=True, text=True,
                        timeout=600)
