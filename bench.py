@@ -592,7 +592,7 @@ def run_ours(a, rank, world, local_rank):
         e2e_s = time.perf_counter() - t0
         sim2.close()
         e2e_value, e2e_s = aggregate_replicas(updates_per_step * a.steps, e2e_s, dist, dev)
-        obs_bytes = len(times) * 72
+        obs_bytes = len(times) * sca.OBS_RECORD_BYTES
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 4 * n_words, "d2h_bytes_per_step": 4 * n_words + obs_bytes,
                "ms_per_step": 1000.0 * e2e_s / a.steps,

@@ -99,6 +99,8 @@ typedef struct sca_obs {
     double w2;         /* num / N^2 rounded to double, for convenience */
     int32_t status;    /* SCA_OK, or SCA_ESTATE if the slopes did not close */
     int32_t reserved;
+    int64_t h00;       /* absolute height of the origin site while sca_track_origin is on (see
+                          there): <h> = h00 + S1 / N is the absolute mean height; 0 otherwise */
 } sca_obs;
 
 /* One exact two-time height correlation (see sca_correlate).  Signed 128-bit values are split
@@ -151,6 +153,18 @@ int sca_observe(sca_sim *sim, sca_obs *out);
  * count) and observe there; one synchronisation at the end.  out[i] receives observation i.
  * Errors: SCA_EINVAL, SCA_ECUDA, SCA_ESTATE (first failing observation's status). */
 int sca_run(sca_sim *sim, const uint64_t *times, uint32_t n, sca_obs *out);
+
+/* Track the absolute height of the origin site (x, y) = (0, 0) through the updates (enable != 0)
+ * or stop (0).  Slopes fix heights only up to a constant; the origin's height, changed by +2
+ * at each deposition there and -2 at each removal (Eq. 1), fixes it, so that every observation
+ * then reports h00 and the absolute mean height <h> = h00 + S1 / N, whose rate of change is the
+ * growth velocity.  Enabling sets the counter to 0: the true absolute height after sca_init or
+ * sca_reset (flat start, h(0,0) = 0), the height relative to the moment of enabling otherwise;
+ * sca_reset and sca_set_state also set it to 0.  Cost: one small launch before each update
+ * launch (it re-runs that launch's MCS on a patch around the origin), and launches of at most
+ * 16 MCS.  Needs a surface state.  Errors: SCA_EINVAL; SCA_ESTATE when the state is not a
+ * surface (the next sca_step reports it). */
+int sca_track_origin(sca_sim *sim, int enable);
 
 /* Two-time height correlation of the current state a (MCS t) with a reference state b of the
  * same lattice, typically a copy of an earlier state (MCS s < t): the paper's aging studies

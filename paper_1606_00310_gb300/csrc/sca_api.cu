@@ -186,8 +186,10 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
     s->part = (ObsPartial *)(s->base + lo.off_part);
     s->res = (ObsDev *)(s->base + lo.off_res);
     s->err = (uint32_t *)(s->base + lo.off_err);
+    s->h00 = (int64_t *)(s->base + lo.off_err + 8);
+    s->track_origin = false;
     {
-        cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(uint32_t), s->stream);
+        cudaError_t e = cudaMemsetAsync(s->err, 0, 16, s->stream);
         if (e != cudaSuccess) {
             sca_free(s);
             return cuda_fail(e, "cudaMemsetAsync");
@@ -209,6 +211,7 @@ int sca_reset(sca_sim *s)
     const size_t half = s->lo.state_bytes / 2;
     cudaError_t e = cudaMemsetAsync(s->buf[s->cur], 0x00, half, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync((char *)s->buf[s->cur] + half, 0xFF, half, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->h00, 0, sizeof(int64_t), s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     s->t = 0;
     s->surface = true;
@@ -403,6 +406,9 @@ int sca::step_impl(sca_sim *s, uint64_t n)
     const bool fused = kern == 2;
     if (kern == 4 && !s->surface)
         return fail(SCA_ESTATE, "the wavefront kernel needs a surface state (every plaquette closes)");
+    if (s->track_origin && !s->surface)
+        return fail(SCA_ESTATE, "tracking the origin's height needs a surface state");
+    if (s->track_origin && tbk > origin_max_k()) tbk = origin_max_k();
     if (kern == 3 || kern == 4) {              // temporal blocking: tbk MCS per launch
         if (s->timing) {
             cudaError_t e = record_event(s);
@@ -412,6 +418,11 @@ int sca::step_impl(sca_sim *s, uint64_t n)
         while (done < n) {
             const uint64_t k = (n - done) < (uint64_t)tbk ? (n - done) : (uint64_t)tbk;
             const uint64_t kk = kern == 3 ? k : wave_pick_k((uint32_t)k, (int)s->R.mode);
+            if (s->track_origin) {           // the launch's MCS re-run around the origin first
+                cudaError_t e = launch_origin_track(s->buf[s->cur], s->L, s->Ly, s->t + done,
+                                                    (uint32_t)(kern == 3 ? k : kk), s->R, s->h00, s->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "origin tracker launch");
+            }
             cudaError_t e = kern == 3
                 ? launch_tblock(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->t + done, (uint32_t)k,
                                 s->R, s->stream)
@@ -440,6 +451,10 @@ int sca::step_impl(sca_sim *s, uint64_t n)
     for (uint64_t i = 0; i < n; ++i) {
         const uint64_t t = s->t + i;
         cudaError_t e;
+        if (s->track_origin) {
+            e = launch_origin_track(s->buf[s->cur], s->L, s->Ly, t, 1u, s->R, s->h00, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "origin tracker launch");
+        }
         if (fused) {
             e = launch_fused_mcs(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, t, s->R, s->err,
                                  s->stream, nullptr, s->fused_V, s->fused_ring);
@@ -493,7 +508,7 @@ int sca_run(sca_sim *s, const uint64_t *times, uint32_t n, sca_obs *out)
             int rc = step_impl(s, times[done + i] - s->t);
             if (rc) return rc;
             cudaError_t e = launch_observe_xy(s->buf[s->cur], s->L, s->Ly, s->part, s->res + i, s->t,
-                                              s->stream);
+                                              s->stream, s->track_origin ? s->h00 : nullptr);
             if (e != cudaSuccess) return cuda_fail(e, "observe launch");
         }
         uint32_t err = 0;
@@ -522,6 +537,15 @@ int sca_observe(sca_sim *s, sca_obs *out)
     if (!s || !out) return fail(SCA_EINVAL, "NULL argument");
     const uint64_t t = s->t;
     return sca_run(s, &t, 1, out);
+}
+
+int sca_track_origin(sca_sim *s, int enable)
+{
+    if (!s) return fail(SCA_EINVAL, "NULL simulation");
+    cudaError_t e = cudaMemsetAsync(s->h00, 0, sizeof(int64_t), s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sca_track_origin");
+    s->track_origin = enable != 0;
+    return SCA_OK;
 }
 
 int sca_correlate(sca_sim *s, const uint32_t *ref_words_dev, sca_corr *out)
@@ -558,6 +582,7 @@ int sca_set_state(sca_sim *s, const uint32_t *host_words, size_t n_words, uint64
     if (n_words * sizeof(uint32_t) != s->lo.state_bytes) return fail(SCA_EINVAL, "wrong word count");
     cudaError_t e = cudaMemcpyAsync(s->buf[s->cur], host_words, s->lo.state_bytes,
                                     cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->h00, 0, sizeof(int64_t), s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sca_set_state");
     bool surf = false;
@@ -580,6 +605,7 @@ int sca_set_state_async(sca_sim *s, const uint32_t *host_words, size_t n_words, 
     }
     cudaError_t e = cudaMemcpyAsync(s->buf[s->cur], host_words, s->lo.state_bytes,
                                     cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->h00, 0, sizeof(int64_t), s->stream);
     if (e == cudaSuccess)
         e = surface_check_async(s->buf[s->cur], s->L, s->Ly, reinterpret_cast<uint32_t *>(s->part), s->chk_host,
                                 s->stream);
@@ -612,7 +638,8 @@ int sca_run_async(sca_sim *s, const uint64_t *times, uint32_t n)
     for (uint32_t i = 0; i < n; ++i) {
         int rc = step_impl(s, times[i] - s->t);
         if (rc) return rc;
-        cudaError_t e = launch_observe_xy(s->buf[s->cur], s->L, s->Ly, s->part, s->res + i, s->t, s->stream);
+        cudaError_t e = launch_observe_xy(s->buf[s->cur], s->L, s->Ly, s->part, s->res + i, s->t, s->stream,
+                                          s->track_origin ? s->h00 : nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "observe launch");
     }
     s->async_obs = n;

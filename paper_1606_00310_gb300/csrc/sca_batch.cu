@@ -790,6 +790,7 @@ __global__ void k_batch_finalize(const BatchLattice *lat, int n_lat, const ObsPa
     o.w2 = 0.0;
     o.status = flags ? -7 : 0;
     o.reserved = (int32_t)flags;
+    o.h00 = 0;
     out[i] = o;
 }
 

@@ -28,6 +28,7 @@ struct ObsDev {
     uint64_t S2_lo, S2_hi, num_lo, num_hi;
     double w2;
     int32_t status, reserved;
+    int64_t h00;        // absolute height of the origin (0 when it is not tracked)
 };
 
 struct ObsPartial {
@@ -112,8 +113,14 @@ int obs_partials(uint32_t rows);
 cudaError_t launch_observe(const uint32_t *A, uint32_t L, int64_t *h0, ObsPartial *partials,
                            ObsDev *result, uint64_t t, cudaStream_t st);
 // The same on an X x Y lattice (X sites per row, Y rows; N = X * Y).
+// h00: the origin-height counter copied into the record (nullptr: 0).
 cudaError_t launch_observe_xy(const uint32_t *A, uint32_t X, uint32_t Y, ObsPartial *partials, ObsDev *result,
-                              uint64_t t, cudaStream_t st);
+                              uint64_t t, cudaStream_t st, const int64_t *h00 = nullptr);
+// Origin-height tracker (sca_origin.cu): re-runs K <= origin_max_k() MCS from the state A (MCS
+// index t0) on a patch around the origin and adds the origin's height change to *h00.
+cudaError_t launch_origin_track(const uint32_t *A, uint32_t X, uint32_t Y, uint64_t t0, uint32_t K, const Rule &R,
+                                int64_t *h00, cudaStream_t st);
+int origin_max_k();
 
 // Two-time height correlation of the states A and B of one X x Y lattice (chunk records in
 // partials, at most obs_partials scratch; result record of corr_record_bytes() bytes).
@@ -148,6 +155,8 @@ struct sca_sim {
     sca::ObsPartial *part;
     sca::ObsDev *res;
     uint32_t *err;      // device word: bit 0 = a kernel wait gave up
+    int64_t *h00;       // device: absolute height of the origin site (tracked when track_origin)
+    bool track_origin;
     cudaStream_t stream;
     bool own_stream;
     uint64_t t;

@@ -269,7 +269,8 @@ __device__ __forceinline__ void block_sum_i128(__int128 &v, __int128 *sh)
 }
 
 __global__ void __launch_bounds__(kObsFinalThreads) k_obs_final(const ObsChunk *chunks, int nchunks,
-                                                                uint32_t L, uint32_t Y, uint64_t t, ObsDev *out)
+                                                                uint32_t L, uint32_t Y, uint64_t t, ObsDev *out,
+                                                                const int64_t *h00)
 {
     __shared__ __int128 sh[32];
     __shared__ int64_t wsum[32];
@@ -316,6 +317,7 @@ __global__ void __launch_bounds__(kObsFinalThreads) k_obs_final(const ObsChunk *
     out->w2 = 0.0;
     out->status = flags ? -7 : 0;   // SCA_ESTATE
     out->reserved = (int32_t)flags;
+    out->h00 = h00 ? *h00 : 0;
 }
 
 // Many lattices: one warp per lattice combines its nch (<= 32) chunk records as k_obs_final
@@ -365,6 +367,7 @@ __global__ void k_obs_final_batch(const ObsChunk *chunks, uint32_t nch, uint32_t
     o.w2 = 0.0;
     o.status = flags ? -7 : 0;   // SCA_ESTATE
     o.reserved = (int32_t)flags;
+    o.h00 = 0;
     out[(size_t)dst[li] * stride] = o;
 }
 
@@ -639,7 +642,7 @@ cudaError_t launch_observe(const uint32_t *A, uint32_t L, int64_t *h0, ObsPartia
 }
 
 cudaError_t launch_observe_xy(const uint32_t *A, uint32_t X, uint32_t Y, ObsPartial *partials, ObsDev *result,
-                              uint64_t t, cudaStream_t st)
+                              uint64_t t, cudaStream_t st, const int64_t *h00)
 {
     const uint32_t W = X / 64;
     const int grid = obs_partials(Y);
@@ -647,7 +650,7 @@ cudaError_t launch_observe_xy(const uint32_t *A, uint32_t X, uint32_t Y, ObsPart
     ObsChunk *chunks = reinterpret_cast<ObsChunk *>(partials);
     if (W % 128 == 0) k_obs_rows<true><<<grid, 32 * kObsRowsWarps, 0, st>>>(A, X, Y, chunks);
     else k_obs_rows<false><<<grid, 32 * kObsRowsWarps, 0, st>>>(A, X, Y, chunks);
-    k_obs_final<<<1, kObsFinalThreads, 0, st>>>(chunks, grid, X, Y, t, result);
+    k_obs_final<<<1, kObsFinalThreads, 0, st>>>(chunks, grid, X, Y, t, result, h00);
     count_launches(2);
     return cudaGetLastError();
 }

@@ -28,7 +28,11 @@ class sca_obs(C.Structure):
     _fields_ = [("t", C.c_uint64), ("N", C.c_uint64), ("S1", C.c_int64),
                 ("S2_lo", C.c_uint64), ("S2_hi", C.c_uint64),
                 ("num_lo", C.c_uint64), ("num_hi", C.c_uint64),
-                ("w2", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32)]
+                ("w2", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("h00", C.c_int64)]
+
+
+OBS_RECORD_BYTES = C.sizeof(sca_obs)
 
 
 class sca_corr(C.Structure):
@@ -63,6 +67,7 @@ SIGNATURES = {
     "sca_run": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.c_uint32, C.POINTER(sca_obs)]),
     "sca_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "sca_correlate": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(sca_corr)]),
+    "sca_track_origin": (C.c_int, [C.c_void_p, C.c_int]),
     "sca_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint64]),
     "sca_state_device": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "sca_time": (C.c_uint64, [C.c_void_p]),
@@ -184,13 +189,14 @@ class Obs:
     num: int
     w2: float
     status: int
+    h00: int = 0          # absolute height of the origin (while tracked; see Sim.track_origin)
 
     @staticmethod
     def from_c(o: sca_obs) -> "Obs":
         return Obs(t=int(o.t), N=int(o.N), S1=int(o.S1),
                    S2=int(o.S2_lo) | (int(o.S2_hi) << 64),
                    num=int(o.num_lo) | (int(o.num_hi) << 64), w2=float(o.w2),
-                   status=int(o.status))
+                   status=int(o.status), h00=int(o.h00))
 
 
 @dataclass
@@ -307,6 +313,10 @@ class Sim:
         if rc not in (OK, ESTATE):
             check(rc, "sca_run")
         return [Obs.from_c(o) for o in out]
+
+    def track_origin(self, enable: bool = True):
+        """Carry the origin's absolute height through the updates (observations report h00)."""
+        check(load().sca_track_origin(self._h, 1 if enable else 0), "sca_track_origin")
 
     def snapshot(self):
         """A device copy (int32 CUDA tensor) of the current canonical words, the reference state

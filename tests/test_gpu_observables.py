@@ -106,3 +106,79 @@ def test_edwards_wilkinson_log_growth(sca):
     assert inc[1:].max() / inc[1:].min() < 1.4, inc
     kinc = np.diff(kpz)
     assert kinc[-1] / kinc[1] > 3.0, kinc
+
+
+# ------------------------------------------------------------------------- origin height
+def _oracle_h00(X, Y, seed, p, q, times, start=None):
+    if start is None:
+        bx, by = o.init_flat_rect(X, Y)
+    else:
+        bx, by = o.unpack_rect(X, Y, start)
+    out, h00, t = [], 0, 0
+    for tt in times:
+        h00 += o.run_rect_counted(bx, by, seed, p, q, t0=t, n_mcs=tt - t)[0]
+        t = tt
+        out.append((h00, o.observe_rect(bx, by)["S1"]))
+    return out
+
+
+@pytest.mark.parametrize("X,Y,p,q,kernel,k", [
+    (256, 256, 0.75, 0.25, 1, None),             # two-pass, one tracker launch per MCS
+    (2048, 2048, 0.5, 0.0, 2, None),             # fused
+    (512, 512, 0.7, 0.3, 3, 32),                 # shared-memory blocking, 32 MCS capped to 16
+    (1024, 1024, 0.625, 0.375, 4, 4),            # height bits, dyadic
+    (192, 66, 0.6, 0.35, 4, 2),                  # height bits, per-site uniforms, X x Y
+    (128, 6, 0.875, 0.125, 0, None),             # few rows: the patch wraps the lattice
+    (4096, 4096, 0.5, 0.5, 0, None),
+])
+def test_origin_height_against_oracle(sca, X, Y, p, q, kernel, k):
+    times = [1, 5, 18, 40]
+    with sca.Sim(X, seed=13, p=p, q=q, Ly=Y) as sim:
+        sim.set_kernel(kernel)
+        if k is not None:
+            sim.set_temporal_block(k)
+        sim.track_origin(True)
+        obs = sim.run(times)
+    ref = _oracle_h00(X, Y, 13, p, q, times)
+    assert [(g.h00, g.S1) for g in obs] == ref
+    assert any(h != 0 for h, _ in ref)
+
+
+def test_origin_height_rough_p1_wavefront(sca):
+    """p = 1 from a rough surface at 16 MCS per launch (the benchmark's kernel): against the
+    oracle, and the absolute mean height identity N h00 + S1 = N/2 + (all height changes)."""
+    L = 2048
+    bx, by = o.init_flat(L)
+    o.run(bx, by, 31, 0.625, 0.375, t0=0, n_mcs=4)
+    start = o.pack(bx, by)
+    times = [16, 33, 64]
+    with sca.Sim(L, seed=5, p=1.0, q=0.0, kernel=sca.KERNEL_WAVE) as sim:
+        sim.set_state(start, t=0)
+        sim.set_temporal_block(16)
+        sim.track_origin(True)
+        obs = sim.run(times)
+    assert [(g.h00, g.S1) for g in obs] == _oracle_h00(L, L, 5, 1.0, 0.0, times, start=start)
+
+
+def test_origin_height_closed_form_large(sca):
+    """L = 65536, p = 1 from flat: every site deposits once per MCS, so h00 = 2t and the
+    absolute mean height h00 + S1/N = 2t + 1/2."""
+    with sca.Sim(65536, seed=1, p=1.0, q=0.0) as sim:
+        sim.track_origin(True)
+        obs = sim.run([1, 16, 40])
+    for g in obs:
+        assert g.h00 == 2 * g.t and 2 * g.S1 == g.N
+
+
+def test_origin_tracking_needs_a_surface(sca):
+    with sca.Sim(512, seed=1, p=0.5, q=0.0) as sim:
+        w = sim.get_state()
+        w[9] ^= 1
+        sim.set_state(w, t=0)
+        sim.set_kernel(sca.KERNEL_TWO_PASS)
+        sim.track_origin(True)
+        with pytest.raises(sca.ScaError) as e:
+            sim.step(1)
+        assert e.value.code == sca.ESTATE
+        sim.track_origin(False)
+        sim.step(1)
