@@ -264,6 +264,26 @@ def oracle_sample(L, p, q, seconds, seed=1, threads=0):
     return updates / dt, cores, desc
 
 
+def bitvec_sample(L, p, q, seconds):
+    """Time the bit-vectorized CPU implementation (w = 64, all host cores; the paper's CPU
+    design, Sec. II.B) on the full L x L lattice from flat, enough MCS for about `seconds`.
+    Returns (updates_per_s, cores, description)."""
+    import cpu_bitvec as bv
+    import oracle as o
+    mode = o.rng_mode(p, q)
+    w = bv.flat_words(L)
+    t0 = time.perf_counter()
+    bv.run(w, L, 1, p, q, mode, t0=0, n_mcs=1)
+    one = time.perf_counter() - t0
+    n = max(1, int(seconds / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    bv.run(w, L, 1, p, q, mode, t0=1, n_mcs=n)
+    dt = time.perf_counter() - t0
+    desc = ("bit-vectorized CPU implementation (64-bit words, OpenMP over rows), full L=%d lattice "
+            "from flat, p=%g q=%g, %d MCS = %.3g site updates in %.1f s" % (L, p, q, n, float(L) * L * n, dt))
+    return float(L) * L * n / dt, bv.threads(), desc
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -695,12 +715,20 @@ def run_ours(a, rank, world, local_rank):
         # of 200/s): latency without the queue of the oversubscribed stream
         serving_light = run_serving(150, a.serve_slots, rate_per_s=15.0)
 
-    cpu = None
+    cpu = cpu_bv = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
         r, cores, desc = oracle_sample(L, a.p, a.q, a.cpu_seconds)
         r1, _, desc1 = oracle_sample(L, a.p, a.q, max(1.0, a.cpu_seconds / 3), threads=1)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                "cpu_model": cpu_model(), "value_1_core": r1, "sample_1_core": desc1}
+        # the like-for-like CPU baseline: the same bit-vectorized update on 64-bit words over
+        # all cores (the paper's CPU implementation), the workload's rule and the paper's p = 1/2
+        bv_rate, bv_cores, bv_desc = bitvec_sample(L, a.p, a.q, a.cpu_seconds)
+        bv_half, _, bv_half_desc = bitvec_sample(L, 0.5, 0.0, a.cpu_seconds)
+        cpu_bv = {"value": bv_rate, "unit": UNIT, "cores": bv_cores, "cpu_model": cpu_model(),
+                  "kind": "bit-vectorized w=64 (paper Sec. II.B CPU implementation)",
+                  "sample": bv_desc, "gpu_over_cpu": value / bv_rate,
+                  "p_half": bv_half, "sample_p_half": bv_half_desc}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -710,6 +738,10 @@ def run_ours(a, rank, world, local_rank):
                 "config": config(a, world), "roofline": roof, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "w2_final": obs[-1].w2}
+        if cpu_bv:
+            if extra:
+                cpu_bv["gpu_over_cpu_p_half"] = extra["value"] / cpu_bv["p_half"]
+            line["cpu_baseline_bitvec"] = cpu_bv
         if extra:
             line["context_p_half"] = extra
         if rough:
