@@ -78,6 +78,9 @@ def lib():
                                               C.c_double, C.c_int, C.c_uint64, C.c_uint64,
                                               C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.oracle_run_rect_counted.restype = C.c_int
+        L.oracle_rs_run_rect.argtypes = [C.c_int64, C.c_int64, u8p, u8p, C.c_uint64, C.c_double,
+                                         C.c_double, C.c_uint64, C.c_uint64]
+        L.oracle_rs_run_rect.restype = C.c_int
         L.oracle_corr_rect.argtypes = [C.c_int64, C.c_int64, u8p, u8p, u8p, u8p,
                                        C.POINTER(C.c_int64), C.POINTER(C.c_int64), i64p, i64p]
         L.oracle_corr_rect.restype = C.c_int
@@ -301,3 +304,10 @@ def run_rect_counted(bx, by, seed, p, q, mode=None, t0=0, n_mcs=1):
                                      C.byref(org), C.byref(tot)) != 0:
         raise ValueError("oracle_run_rect_counted: bad parameters")
     return int(org.value), int(tot.value)
+
+
+def rs_run(bx, by, seed, p, q, t0=0, n_mcs=1):
+    """Random-sequential dynamics over the 4 x 4 words (see sca_oracle.c) on (Y, X) arrays."""
+    Y, X = bx.shape
+    if lib().oracle_rs_run_rect(X, Y, bx, by, seed, float(p), float(q), t0, n_mcs) != 0:
+        raise ValueError("oracle_rs_run_rect: bad parameters")

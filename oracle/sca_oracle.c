@@ -392,6 +392,61 @@ int oracle_observe(int64_t L, const uint8_t *bx, const uint8_t *by,
     return oracle_observe_rect(L, L, bx, by, S1_out, S2_out, num_out);
 }
 
+/* ------------------------------------------------------------------------------------------
+ * Random-sequential (RS) dynamics on the local encoding (Sec. II.A: 4 x 4 sites per 32-bit
+ * word, the encoding of choice when sites are selected at random; the paper's non-vectorized
+ * comparison).  Reading (the paper gives no schedule for it): random-sequential updates
+ * decomposed over the 4 x 4 words.  Word (wx, wy) holds the sites 4 wx <= x < 4 wx + 4,
+ * 4 wy <= y < 4 wy + 4 (X, Y multiples of 8).  One MCS is two phases; in phase ph the words with
+ * (wx + wy) & 1 == ph are active (no two active sites are neighbours, so the active words
+ * evolve independently and in any order); an active word receives 16 attempts in sequence
+ * a = 0..15 (on average one per site and MCS).  Attempt a of word w = wy * (X/4) + wx in
+ * phase ph of MCS t takes the Philox4x32-10 call with counter
+ *     (w low 32, t low 32, ph | a << 1 | (t >> 32) << 6, 2 | (w >> 32) << 2)
+ * and key (seed low, seed high): the site is i = out[0] >> 28, (x, y) = (4 wx + (i & 3),
+ * 4 wy + (i >> 2)); a local minimum deposits iff out[1] < floor(p 2^32), a local maximum is
+ * removed iff out[1] < floor(q 2^32) (Eq. 1).  On a 4 x 4 torus (one word) this is plain
+ * random-sequential dynamics, 16 uniform site choices per MCS.
+ * ---------------------------------------------------------------------------------------- */
+int oracle_rs_run_rect(int64_t X, int64_t Y, uint8_t *bx, uint8_t *by, uint64_t seed, double p, double q,
+                       uint64_t t0, uint64_t n_mcs)
+{
+    if (X < 4 || Y < 4 || (X % 4) || (Y % 4)) return -1;
+    if ((X > 4 && X % 8) || (Y > 4 && Y % 8)) return -1;
+    if (!(p >= 0.0 && p <= 1.0 && q >= 0.0 && q <= 1.0)) return -1;
+    const uint64_t Tp = (uint64_t)floor(ldexp(p, 32)), Tq = (uint64_t)floor(ldexp(q, 32));
+    const int64_t WX = X / 4, WY = Y / 4;
+    const uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    for (uint64_t t = t0; t < t0 + n_mcs; t++) {
+        for (int ph = 0; ph <= 1; ph++) {
+            #pragma omp parallel for schedule(static)
+            for (int64_t wy = 0; wy < WY; wy++)
+                for (int64_t wx = 0; wx < WX; wx++) {
+                    if (((wx + wy) & 1) != ph) continue;
+                    const uint64_t w = (uint64_t)(wy * WX + wx);
+                    for (int a = 0; a < 16; a++) {
+                        uint32_t ctr[4] = { (uint32_t)w, (uint32_t)t,
+                                            (uint32_t)ph | ((uint32_t)a << 1) | ((uint32_t)(t >> 32) << 6),
+                                            2u | ((uint32_t)(w >> 32) << 2) };
+                        uint32_t out[4];
+                        oracle_philox4x32_10(ctr, key, out);
+                        const int i = (int)(out[0] >> 28);
+                        const int64_t x = 4 * wx + (i & 3), y = 4 * wy + (i >> 2);
+                        const int64_t xr = (x + 1) % X, yu = (y + 1) % Y;
+                        uint8_t *sa = &bx[y * X + x], *sb = &by[y * X + x];
+                        uint8_t *sc = &bx[y * X + xr], *sd = &by[yu * X + x];
+                        const int is_min = (*sa == 0 && *sb == 0 && *sc == 1 && *sd == 1);
+                        const int is_max = (*sa == 1 && *sb == 1 && *sc == 0 && *sd == 0);
+                        if ((is_min && (uint64_t)out[1] < Tp) || (is_max && (uint64_t)out[1] < Tq)) {
+                            *sa ^= 1; *sb ^= 1; *sc ^= 1; *sd ^= 1;
+                        }
+                    }
+                }
+        }
+    }
+    return 0;
+}
+
 /* Two-time height correlation of two states of the same X x Y lattice (the paper's two-time
  * functions and aging studies, Sec. I and Sec. IV; definition here): with heights h_a, h_b of
  * the two states (each from h(0,0) = 0, as in oracle_heights_rect),

@@ -5,7 +5,8 @@ neighbour index, a dropped condition, swapped sublattice order, an off-by-one or
 order in the dyadic construction, a wrong Philox operand, a non-strict threshold, a wrong height
 path, a wrong packed offset, a missing flip, a missing counter field, q replaced by p, and on X x Y
 lattices a row count and a row length confused with each other, a wrong factor or sign in the
-two-time correlation, the origin's height change counted at a neighbour or with the wrong sign)
+two-time correlation, the origin's height change counted at a neighbour or with the wrong sign; in the random-
+sequential dynamics the site from the wrong bits, the wrong active words, too few attempts)
 and runs
 the oracle pin tests against the mutant.  CPU only; the GPU library is not involved.
 """
@@ -56,6 +57,10 @@ MUTANTS = {
     # origin height counter
     "origin_counts_a_neighbour": ("if (x == 0 && y == 0) org += dh;", "if (x == 1 && y == 0) org += dh;"),
     "height_change_sign_of_removal": ("return is_min ? 2 : -2;", "return 2;"),
+    # random-sequential dynamics on the 4 x 4 words
+    "rs_site_from_low_bits": ("const int i = (int)(out[0] >> 28);", "const int i = (int)(out[0] & 15);"),
+    "rs_active_words_in_columns": ("if (((wx + wy) & 1) != ph) continue;", "if ((wx & 1) != ph) continue;"),
+    "rs_eight_attempts": ("for (int a = 0; a < 16; a++) {", "for (int a = 0; a < 8; a++) {"),
     # two-time correlation
     "corr_product_uses_a_twice": ("Sab += (__int128)ha[i] * hb[i];", "Sab += (__int128)ha[i] * ha[i];"),
     "corr_numerator_sign": ("__int128 cnum = (__int128)n * Sab - Sa * Sb;",
@@ -73,6 +78,8 @@ CORR_ONLY = {"corr_product_uses_a_twice", "corr_numerator_sign"}
 CORR_PINS = ["tests/test_oracle_corr.py"]
 HEIGHT_ONLY = {"origin_counts_a_neighbour", "height_change_sign_of_removal"}
 HEIGHT_PINS = ["tests/test_oracle_height.py"]
+RS_ONLY = {"rs_site_from_low_bits", "rs_active_words_in_columns", "rs_eight_attempts"}
+RS_PINS = ["tests/test_oracle_rs.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -87,7 +94,7 @@ def test_mutant_is_caught(name, tmp_path):
                     ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutants.py"))
     shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
     pins = (RECT_PINS if name in RECT_ONLY else CORR_PINS if name in CORR_ONLY else
-            HEIGHT_PINS if name in HEIGHT_ONLY else PIN_TESTS)
+            HEIGHT_PINS if name in HEIGHT_ONLY else RS_PINS if name in RS_ONLY else PIN_TESTS)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         *pins], cwd=str(tmp_path), capture_output=True, text=True,
                        timeout=600)
