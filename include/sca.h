@@ -84,8 +84,25 @@ typedef struct sca_params {
                         2 <= Ly <= 131072.  X != Y runs on the two-pass kernel (1) and the
                         wavefront kernel (4) of sca_set_kernel; batches, servers and
                         sca_observe_noalloc take square lattices only */
-    uint32_t reserved;  /* 0 */
+    uint32_t dynamics;  /* SCA_DYN_SCA (0): the stochastic cellular automaton of the paper;
+                           SCA_DYN_RANDOM_SEQUENTIAL (1): its non-vectorized comparison (see
+                           there); single lattices only (batches and servers refuse it) */
 } sca_params;
+
+/* ---- dynamics ------------------------------------------------------------------------------- */
+#define SCA_DYN_SCA 0   /* sublattice-parallel updates, even sites then odd (Sec. I.A) */
+/* Random-sequential updates on the local encoding (Sec. II.A: 4 x 4 sites per 32-bit word, the
+ * encoding of choice when sites are selected at random; Sec. III benchmarks it against the
+ * bit-vectorized SCA).  The paper gives no schedule; this library's: the words hold the
+ * 4 x 4 tiles 4 wx <= x < 4 wx + 4, 4 wy <= y < 4 wy + 4; each MCS is two phases over the
+ * checkerboard of words ((wx + wy) & 1 == phase; active words share no bond), and an active
+ * word w = wy * (X/4) + wx takes 16 attempts in sequence: attempt a of MCS t, phase ph, uses the
+ * Philox4x32-10 call with counter (w, t, ph | a << 1 | (t >> 32) << 6, 2), picks site
+ * out[0] >> 28 (column & 3, row >> 2 of the tile) and flips it if it is a local minimum and
+ * out[1] < floor(p 2^32) or a local maximum and out[1] < floor(q 2^32).  On a 4 x 4 torus this
+ * is plain random-sequential dynamics.  Needs Y a multiple of 8 (X is a multiple of 64).  The
+ * state on this ABI stays the canonical words; sca_track_origin is not available. */
+#define SCA_DYN_RANDOM_SEQUENTIAL 1
 
 /* One exact roughness observation. */
 typedef struct sca_obs {
@@ -244,7 +261,7 @@ int sca_set_temporal_block(sca_sim *sim, int mcs_per_launch);
 /* Row bands of the register-wavefront kernel (kernel 4): the lattice is cut into `bands` bands
  * of rows times columns of 30 packed words, one warp per tile; 0 = automatic (enough tiles for
  * one full wave of resident warps).  Results do not depend on it.  Errors: SCA_EINVAL unless
- * 0 <= bands <= L/2. */
+ * 0 <= bands <= Y/2. */
 int sca_set_wave_bands(sca_sim *sim, int bands);
 
 /* Launch shape of the fused kernel: words_per_thread (1, 2 or 4; the CTA has L/64 /
@@ -255,7 +272,8 @@ int sca_set_wave_bands(sca_sim *sim, int bands);
 int sca_set_fused_shape(sca_sim *sim, int words_per_thread, int ring);
 
 /* Update kernel the simulation uses now (1 = two-pass, 2 = fused, 3 = temporal blocking in
- * shared memory, 4 = register-wavefront temporal blocking), after automatic choice. */
+ * shared memory, 4 = register-wavefront temporal blocking), after automatic choice; 5 for the
+ * random-sequential dynamics (sca_params.dynamics = 1, which ignores the kernel choice). */
 int sca_get_kernel(const sca_sim *sim);
 
 /* Kernel timing: while enabled, the library records a CUDA event pair on the simulation's

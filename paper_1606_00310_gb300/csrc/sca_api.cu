@@ -133,6 +133,9 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
     Rule R;
     int rc = make_rule(*params, R);
     if (rc) return rc;
+    if (params->dynamics > SCA_DYN_RANDOM_SEQUENTIAL) return fail(SCA_EINVAL, "unknown dynamics");
+    if (params->dynamics == SCA_DYN_RANDOM_SEQUENTIAL && !rs_supported(params->L, Y))
+        return fail(SCA_EINVAL, "random-sequential dynamics needs Y a multiple of 8");
     if (dev_buf) {
         if (dev_buf_bytes < lo.total) return fail(SCA_EINVAL, "device buffer too small");
         if ((uintptr_t)dev_buf % 256 != 0) return fail(SCA_EINVAL, "device buffer not 256-byte aligned");
@@ -142,6 +145,9 @@ int sca_init(const sca_params *params, void *stream, void *dev_buf, size_t dev_b
     s->L = params->L;
     s->W = params->L / 64;
     s->Ly = Y;
+    s->dynamics = params->dynamics;
+    s->rs_Tp = (uint64_t)std::floor(std::ldexp(params->p, 32));
+    s->rs_Tq = (uint64_t)std::floor(std::ldexp(params->q, 32));
     s->lo = lo;
     s->t = 0;
     s->kernel = 0;
@@ -389,6 +395,7 @@ int sca_set_fused_shape(sca_sim *s, int words_per_thread, int ring)
 int sca_get_kernel(const sca_sim *s)
 {
     if (!s) return fail(SCA_EINVAL, "NULL simulation");
+    if (s->dynamics == SCA_DYN_RANDOM_SEQUENTIAL) return 5;
     int rc = resolve_surface(const_cast<sca_sim *>(s));
     if (rc) return rc;
     return effective_kernel(s, nullptr);
@@ -400,6 +407,22 @@ int sca::step_impl(sca_sim *s, uint64_t n)
     {
         int rc = resolve_surface(s);
         if (rc) return rc;
+    }
+    if (s->dynamics == SCA_DYN_RANDOM_SEQUENTIAL) {  // in place, the other buffer as local words
+        if (s->timing) {
+            cudaError_t e = record_event(s);
+            if (e != cudaSuccess) return cuda_fail(e, "timing event");
+        }
+        cudaError_t e = launch_rs(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->Ly, s->t, n, s->R, s->rs_Tp,
+                                  s->rs_Tq, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "random-sequential launch");
+        s->t += n;
+        if (s->timing) {
+            s->timed_launches += 2 * n;
+            e = record_event(s);
+            if (e != cudaSuccess) return cuda_fail(e, "timing event");
+        }
+        return SCA_OK;
     }
     int tbk = 0;
     const int kern = effective_kernel(s, &tbk);
@@ -542,6 +565,8 @@ int sca_observe(sca_sim *s, sca_obs *out)
 int sca_track_origin(sca_sim *s, int enable)
 {
     if (!s) return fail(SCA_EINVAL, "NULL simulation");
+    if (enable && s->dynamics != SCA_DYN_SCA)
+        return fail(SCA_EINVAL, "the origin's height is tracked for the SCA dynamics only");
     cudaError_t e = cudaMemsetAsync(s->h00, 0, sizeof(int64_t), s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sca_track_origin");
     s->track_origin = enable != 0;

@@ -1206,6 +1206,10 @@ int sca_batch_init(const sca_params *params, uint32_t count, void *stream, sca_b
             delete b;
             return fail(SCA_EINVAL, "batch lattices are square (Ly = 0 or L)");
         }
+        if (params[i].dynamics != SCA_DYN_SCA) {
+            delete b;
+            return fail(SCA_EINVAL, "batch lattices run the SCA dynamics");
+        }
         BatchLattice &lt = b->lat[i];
         std::memset(&lt, 0, sizeof(lt));
         int rc = make_rule(params[i], lt.R);

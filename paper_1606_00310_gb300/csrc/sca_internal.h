@@ -121,6 +121,11 @@ cudaError_t launch_observe_xy(const uint32_t *A, uint32_t X, uint32_t Y, ObsPart
 cudaError_t launch_origin_track(const uint32_t *A, uint32_t X, uint32_t Y, uint64_t t0, uint32_t K, const Rule &R,
                                 int64_t *h00, cudaStream_t st);
 int origin_max_k();
+// Random-sequential dynamics on the local 4 x 4 encoding (sca_rs.cu): n_mcs MCS on the
+// canonical words A in place, Lw (X Y / 4 bytes) the local-encoding buffer.
+cudaError_t launch_rs(uint32_t *A, uint32_t *Lw, uint32_t X, uint32_t Y, uint64_t t0, uint64_t n_mcs,
+                      const Rule &R, uint64_t Tp, uint64_t Tq, cudaStream_t st);
+bool rs_supported(uint32_t X, uint32_t Y);
 
 // Two-time height correlation of the states A and B of one X x Y lattice (chunk records in
 // partials, at most obs_partials scratch; result record of corr_record_bytes() bytes).
@@ -157,6 +162,8 @@ struct sca_sim {
     uint32_t *err;      // device word: bit 0 = a kernel wait gave up
     int64_t *h00;       // device: absolute height of the origin site (tracked when track_origin)
     bool track_origin;
+    uint32_t dynamics;  // SCA_DYN_*
+    uint64_t rs_Tp, rs_Tq;   // random-sequential acceptance thresholds floor(p 2^32), floor(q 2^32)
     cudaStream_t stream;
     bool own_stream;
     uint64_t t;

@@ -400,6 +400,7 @@ static int submit_impl(sca_server *srv, const sca_params *params, uint64_t n_mcs
     if (params->L > srv->max_L) return fail(SCA_EINVAL, "L exceeds the server's maximum");
     if (params->Ly != 0 && params->Ly != params->L)
         return fail(SCA_EINVAL, "served lattices are square (Ly = 0 or L)");
+    if (params->dynamics != SCA_DYN_SCA) return fail(SCA_EINVAL, "served lattices run the SCA dynamics");
     const size_t need = sca_workspace_bytes(params->L);
     if (need == 0) return fail(SCA_EINVAL, "L must be a multiple of 64 in [64, 131072]");
     if (need + 256 > srv->budget) return fail(SCA_EBUDGET, "request state exceeds the device budget");

@@ -17,11 +17,13 @@ OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT, EBUSY, ESTATE, ENOTFOUND, ECANCELE
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 RNG_AUTO, RNG_DYADIC, RNG_UNIFORM32 = 0, 1, 2
 KERNEL_AUTO, KERNEL_TWO_PASS, KERNEL_FUSED, KERNEL_TBLOCK, KERNEL_WAVE = 0, 1, 2, 3, 4
+KERNEL_RANDOM_SEQUENTIAL = 5          # reported by kernel_in_use() for DYN_RANDOM_SEQUENTIAL
+DYN_SCA, DYN_RANDOM_SEQUENTIAL = 0, 1
 
 
 class sca_params(C.Structure):
     _fields_ = [("L", C.c_uint32), ("rng", C.c_uint32), ("seed", C.c_uint64),
-                ("p", C.c_double), ("q", C.c_double), ("Ly", C.c_uint32), ("reserved", C.c_uint32)]
+                ("p", C.c_double), ("q", C.c_double), ("Ly", C.c_uint32), ("dynamics", C.c_uint32)]
 
 
 class sca_obs(C.Structure):
@@ -242,7 +244,7 @@ class Sim:
     stream of the current device); all of the simulation's kernels run on it."""
 
     def __init__(self, L, seed=1, p=1.0, q=0.0, rng=RNG_AUTO, stream=None, workspace=None,
-                 kernel=KERNEL_AUTO, Ly=None):
+                 kernel=KERNEL_AUTO, Ly=None, dynamics=DYN_SCA):
         import torch
         lib = load()
         self.L = int(L)
@@ -260,12 +262,12 @@ class Sim:
             stream.wait_stream(torch.cuda.current_stream())   # workspace allocation order
         self.stream = stream
         prm = sca_params(L=self.L, rng=rng, seed=seed, p=p, q=q,
-                         Ly=0 if self.Ly == self.L else self.Ly)
+                         Ly=0 if self.Ly == self.L else self.Ly, dynamics=int(dynamics))
         h = C.c_void_p()
         check(lib.sca_init(C.byref(prm), C.c_void_p(self.stream.cuda_stream),
                            C.c_void_p(workspace.data_ptr()), nbytes, C.byref(h)), "sca_init")
         self._h = h
-        self.params = dict(L=self.L, Ly=self.Ly, seed=seed, p=p, q=q, rng=rng)
+        self.params = dict(L=self.L, Ly=self.Ly, seed=seed, p=p, q=q, rng=rng, dynamics=int(dynamics))
         if kernel != KERNEL_AUTO:
             self.set_kernel(kernel)
 
