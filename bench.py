@@ -40,6 +40,26 @@ BYTES_PER_UPDATE = 0.5   # each slope bit read once and written once per MCS (ro
 # half-step, two 3-input logic ops fold the four neighbour comparisons, one applies the flip,
 # one funnel shift aligns the offset x-neighbour: 4 ALU-pipe ops per 32 site updates.
 WAVE_ALU_OPS_PER_UPDATE = 4.0 / 32.0
+# Paths that draw random numbers are bound by issue slots shared by the Philox rounds and the
+# logic of the update: time per update = (Philox calls per update) / (measured Philox calls/s)
+# + (logic ops per update outside Philox) / (measured logic ops/s), counts read off the source:
+# - p = 1/2 on the height-bit kernel (four words per lane): one Philox call per lane, half-step
+#   and 128 sites; the update takes 5 logic ops per 32-site word (two three-input ops folding
+#   the four neighbour comparisons, one combining them with the draw, the flip, the funnel
+#   shift of the offset neighbour);
+# - per-site uniforms on the two-pass kernel: one call per 4 sites; per site two threshold
+#   compares with their bit packing (about 5 ops), plus the word's mask and its four XORs
+#   (about 12 ops per 32 sites).
+P_HALF_CALLS_PER_UPDATE = 1.0 / 128.0
+P_HALF_OPS_PER_UPDATE = 5.0 / 32.0
+UNIFORM_CALLS_PER_UPDATE = 1.0 / 4.0
+UNIFORM_OPS_PER_UPDATE = 5.0 + 12.0 / 32.0
+
+
+def issue_bound(calls_per_update, ops_per_update, philox_rate, logic_rate):
+    """Updates per second if the GPU did nothing but the path's Philox calls and logic ops at
+    their measured rates, one after the other."""
+    return 1.0 / (calls_per_update / philox_rate + ops_per_update / logic_rate)
 ALU_LANES_PER_SM = 64    # 32-bit logic / shift results per clock per SM (4 SMSPs x 16 lanes)
 
 
@@ -477,6 +497,10 @@ def run_ours(a, rank, world, local_rank):
         logic_rate = sca.measure_logic_rate()
     except Exception:
         logic_rate = None
+    try:
+        mul_rate, philox_rate = sca.measure_mul_rate()
+    except Exception:
+        mul_rate = philox_rate = None
     for _ in range(a.warmup):
         step()
     vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
@@ -642,14 +666,56 @@ def run_ours(a, rank, world, local_rank):
         half.close()
         del half
         rate = L * L * n_half / (hms / 1000.0)
+        bound = issue_bound(P_HALF_CALLS_PER_UPDATE, P_HALF_OPS_PER_UPDATE, philox_rate, logic_rate) \
+            if philox_rate and logic_rate else None
         extra = {"workload": "L=65536 p=1/2 q=0 (paper Sec. III headline case), %d MCS" % n_half,
                  "value": rate, "unit": UNIT,
+                 "roofline": {"bound": "issue: Philox calls + logic ops (measured rates)",
+                              "achieved": rate, "peak": bound, "unit": UNIT,
+                              "frac": rate / bound if bound else None,
+                              "philox_calls_per_update": P_HALF_CALLS_PER_UPDATE,
+                              "logic_ops_per_update": P_HALF_OPS_PER_UPDATE,
+                              "philox_calls_per_s_measured": philox_rate,
+                              "logic_ops_per_s_measured": logic_rate,
+                              "wide_mul_per_s_measured": mul_rate},
                  "paper_titan_black_updates_per_s": 2.29e11,
                  "ratio_to_paper": rate / 2.29e11,
                  "kernel": h_kern, "launches": h_launches,
                  # the canonical state read and written once per launch, over the launch time
                  "hbm_frac_state_once_per_launch":
                      BYTES_PER_UPDATE * L * L * h_launches / (h_upd_ms / 1000.0) / 1e9 / peak}
+
+    # context: non-dyadic p (per-site 32-bit uniforms, the paper's arbitrary-p case and the
+    # serving workload's rule) at the benchmark's size
+    uni = None
+    if not a.no_extra and rank == 0 and world == 1 and (a.p, a.q) == (1.0, 0.0):
+        us = sca.Sim(L, seed=1, p=0.7, q=0.3, stream=stream)
+        us.step(2)
+        torch.cuda.synchronize(dev)
+        n_u = 8
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        us.step(n_u)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        u_rate = L * L * n_u / (e0.elapsed_time(e1) / 1000.0)
+        u_kern = us.kernel_in_use()
+        us.close()
+        del us
+        bound = issue_bound(UNIFORM_CALLS_PER_UPDATE, UNIFORM_OPS_PER_UPDATE, philox_rate, logic_rate) \
+            if philox_rate and logic_rate else None
+        uni = {"workload": "L=%d p=0.7 q=0.3 (per-site 32-bit uniforms), %d MCS" % (L, n_u),
+               "value": u_rate, "unit": UNIT, "kernel": u_kern,
+               "roofline": {"bound": "issue: Philox calls + logic ops (measured rates)",
+                            "achieved": u_rate, "peak": bound, "unit": UNIT,
+                            "frac": u_rate / bound if bound else None,
+                            "philox_calls_per_update": UNIFORM_CALLS_PER_UPDATE,
+                            "logic_ops_per_update": UNIFORM_OPS_PER_UPDATE,
+                            "philox_calls_per_s_measured": philox_rate,
+                            "logic_ops_per_s_measured": logic_rate,
+                            "philox_only_bound": UNIFORM_CALLS_PER_UPDATE ** -1 * philox_rate
+                            if philox_rate else None}}
 
     # context: the same rule and kernel from a rough surface (a flat surface is a fixed point of
     # p = 1; the kernel's work does not depend on the state, and this measures it)
@@ -744,6 +810,8 @@ def run_ours(a, rank, world, local_rank):
             line["cpu_baseline_bitvec"] = cpu_bv
         if extra:
             line["context_p_half"] = extra
+        if uni:
+            line["context_uniform"] = uni
         if rough:
             line["context_rough_p1"] = rough
         if wide:

@@ -21,6 +21,9 @@
 namespace sca {
 
 constexpr int kRsThreads = 256;
+// Draws made ahead of the attempts they decide: all 16 of a word (2.51e11 attempts/s at
+// L = 16384, against 2.31e11 for groups of 8, 2.28e11 of 4 and 2.21e11 one at a time).
+constexpr int kRsDraws = 16;
 
 // canonical -> local: one thread per local word
 __global__ void k_rs_to_local(const uint32_t *A, uint32_t *Lw, uint32_t X, uint32_t Y)
@@ -90,23 +93,36 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_phase(const RsArgs a)
         uint32_t own = a.Lw[w];
         const uint32_t r0 = a.Lw[wr], u0 = a.Lw[wu];
         uint32_t rgt = r0, up = u0;
-        for (uint32_t at = 0; at < 16; ++at) {
-            const Ctr4 o = philox4x32_10_rk(Ctr4{w, (uint32_t)a.t, (uint32_t)a.ph | (at << 1) | ((uint32_t)(a.t >> 32) << 6),
-                                                 2u},
-                                            a.rk);
-            const uint32_t si = o.x >> 28, lx = si & 3u, ly = si >> 2;
-            const uint32_t pa = 2 * (4 * ly + lx);                         // sx-, sy- of the site
-            const uint32_t pc = lx < 3 ? pa + 2 : 2 * (4 * ly);            // sx- of the right site
-            const uint32_t pd = ly < 3 ? pa + 8 + 1 : 2 * lx + 1;          // sy- of the upper site
-            const uint32_t &cw = lx < 3 ? own : rgt;
-            const uint32_t &dw = ly < 3 ? own : up;
-            const uint32_t sa = (own >> pa) & 1u, sb = (own >> (pa + 1)) & 1u;
-            const uint32_t sc = (cw >> pc) & 1u, sd = (dw >> pd) & 1u;
-            const bool mn = !sa && !sb && sc && sd, mx = sa && sb && !sc && !sd;
-            if ((mn && (uint64_t)o.y < a.Tp) || (mx && (uint64_t)o.y < a.Tq)) {
-                own ^= 3u << pa;
-                if (lx < 3) own ^= 1u << pc; else rgt ^= 1u << pc;
-                if (ly < 3) own ^= 1u << pd; else up ^= 1u << pd;
+        // the draws do not depend on the state: they are made ahead as independent Philox
+        // chains, then applied in attempt order
+#pragma unroll 1
+        for (uint32_t a0 = 0; a0 < 16; a0 += kRsDraws) {
+            uint32_t ox[kRsDraws], oy[kRsDraws];
+#pragma unroll
+            for (int j = 0; j < kRsDraws; ++j) {
+                const uint32_t at = a0 + (uint32_t)j;
+                const Ctr4 o = philox4x32_10_rk(
+                    Ctr4{w, (uint32_t)a.t, (uint32_t)a.ph | (at << 1) | ((uint32_t)(a.t >> 32) << 6), 2u}, a.rk);
+                ox[j] = o.x;
+                oy[j] = o.y;
+            }
+#pragma unroll
+            for (int j = 0; j < kRsDraws; ++j) {
+                const Ctr4 o{ox[j], oy[j], 0u, 0u};
+                const uint32_t si = o.x >> 28, lx = si & 3u, ly = si >> 2;
+                const uint32_t pa = 2 * (4 * ly + lx);                         // sx-, sy- of the site
+                const uint32_t pc = lx < 3 ? pa + 2 : 2 * (4 * ly);            // sx- of the right site
+                const uint32_t pd = ly < 3 ? pa + 8 + 1 : 2 * lx + 1;          // sy- of the upper site
+                const uint32_t &cw = lx < 3 ? own : rgt;
+                const uint32_t &dw = ly < 3 ? own : up;
+                const uint32_t sa = (own >> pa) & 1u, sb = (own >> (pa + 1)) & 1u;
+                const uint32_t sc = (cw >> pc) & 1u, sd = (dw >> pd) & 1u;
+                const bool mn = !sa && !sb && sc && sd, mx = sa && sb && !sc && !sd;
+                if ((mn && (uint64_t)o.y < a.Tp) || (mx && (uint64_t)o.y < a.Tq)) {
+                    own ^= 3u << pa;
+                    if (lx < 3) own ^= 1u << pc; else rgt ^= 1u << pc;
+                    if (ly < 3) own ^= 1u << pd; else up ^= 1u << pd;
+                }
             }
         }
         a.Lw[w] = own;
@@ -124,7 +140,7 @@ static int rs_grid(size_t n)
     return (int)(g < cap ? (g ? g : 1) : cap);
 }
 
-// n_mcs MCS of random-sequential dynamics on the canonical words A, with Lw (X Y / 16 bytes) as
+// n_mcs MCS of random-sequential dynamics on the canonical words A, with Lw (X Y / 4 bytes) as
 // the local-encoding buffer: A -> Lw, the phases, Lw -> A.
 cudaError_t launch_rs(uint32_t *A, uint32_t *Lw, uint32_t X, uint32_t Y, uint64_t t0, uint64_t n_mcs,
                       const Rule &R, uint64_t Tp, uint64_t Tq, cudaStream_t st)
