@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsca.so")
-SOURCES = ["sca_update.cu", "sca_fused.cu", "sca_observe.cu", "sca_api.cu", "sca_noalloc.cu", "sca_batch.cu", "sca_serve.cu", "sca_wave.cu",
+SOURCES = ["sca_update.cu", "sca_fused.cu", "sca_observe.cu", "sca_api.cu", "sca_noalloc.cu", "sca_batch.cu", "sca_batch_api.cu", "sca_serve.cu", "sca_wave.cu",
            "sca_wave_dyadic.cu", "sca_wave_batch.cu", "sca_wave_uniform.cu", "sca_origin.cu",
            "sca_rs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
