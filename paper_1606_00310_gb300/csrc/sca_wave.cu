@@ -107,6 +107,35 @@ static bool wave_plan(uint32_t X, uint32_t Y, uint32_t k, int mode, uint32_t ban
     return true;
 }
 
+#ifndef SCA_WAVE_TAIL_PCT
+#define SCA_WAVE_TAIL_PCT 10
+#endif
+#ifndef SCA_WAVE_TAIL_DIV
+#define SCA_WAVE_TAIL_DIV 2
+#endif
+
+// Two tiers of bands for the planned one-wave launch of the {0, 1}-probability kernel: warps
+// with equal work finish unevenly (an SM quarter's schedulers favour its oldest warps), so the
+// first wave's nb bands share all rows but SCA_WAVE_TAIL_PCT percent of them, and bands
+// SCA_WAVE_TAIL_DIV times shorter, queued after them, take the rest and start in the slots the
+// first finishers free.  10 % in half-height bands: +2.9 % per benchmark step at L = 65536 and
+// +3.4 % at L = 131072 (8 % or 12 % of the rows, or third-height bands, lose against it); at
+// L <= 32768 the short bands would fall under 8 MCS-lengths of rows and the plan stays one
+// tier.  With random draws the kernels run several waves of shorter launches, and a second
+// tier lost 1-7 % (p = 1/2), so they keep one tier.
+static void wave_tiers(uint32_t Y, uint32_t k, int mode, uint32_t *nb, uint32_t *ntall, uint32_t *ytall)
+{
+    if (SCA_WAVE_TAIL_PCT <= 0 || mode != 0) return;
+    const uint32_t rest = 2u * (uint32_t)((uint64_t)Y * SCA_WAVE_TAIL_PCT / 200u);
+    const uint32_t top = Y - rest;
+    const uint32_t tall_h = top / *nb, short_h = tall_h / SCA_WAVE_TAIL_DIV;
+    if (rest == 0 || short_h < 8u * k || short_h < 2) return;
+    const uint32_t nshort = (rest + short_h - 1) / short_h;
+    *ntall = *nb;
+    *ytall = top;
+    *nb += nshort;
+}
+
 bool wave_supported(uint32_t L, uint32_t k, int mode) { return wave_supported_xy(L, L, k, mode); }
 
 bool wave_supported_xy(uint32_t X, uint32_t Y, uint32_t k, int mode)
@@ -129,7 +158,9 @@ cudaError_t launch_wave_xy(const uint32_t *src, uint32_t *dst, uint32_t X, uint3
     if (!wave_plan(X, Y, k, mode, bands, 1, &nb, &nc)) return cudaErrorInvalidValue;
     const int V = wave_V(X, mode, k);
     if (!wave_plan(X, Y, k, mode, bands, blocks_for((int)k, V, R), &nb, &nc)) return cudaErrorInvalidValue;
-    const WaveArgs a{src, dst, X, X / 64, Y, nb, nc, t0, t_dev, R};
+    uint32_t ntall = nb, ytall = Y;
+    if (bands == 0) wave_tiers(Y, k, mode, &nb, &ntall, &ytall);
+    const WaveArgs a{src, dst, X, X / 64, Y, nb, nc, ntall, ytall, t0, t_dev, R};
     const uint64_t tiles = (uint64_t)nb * nc;
     const int grid = (int)((tiles + kWaveWarps - 1) / kWaveWarps);
     count_launches(1);

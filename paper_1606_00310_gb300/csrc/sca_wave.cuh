@@ -39,6 +39,7 @@ struct WaveArgs {
     uint32_t L, W;           // sites per row (X) and words per sublattice row
     uint32_t Y;              // rows
     uint32_t nbands, ncols;  // tiles: bands of rows x columns of words
+    uint32_t ntall, ytall;   // the first ntall bands share rows [0, ytall), the rest [ytall, Y)
     uint64_t t0;             // MCS index of the first step, or offset from *t_dev
     const uint64_t *t_dev;
     Rule R;
@@ -446,8 +447,13 @@ __global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) 
     const uint32_t L = a.L, W = a.W, Y = a.Y;   // L sites per row, Y rows
     // band rows [y0, y1), y0 even: the first streamed row is even, so band-row parity is
     // lattice-row parity
-    const uint32_t y0 = 2u * (uint32_t)(((uint64_t)band * (Y / 2)) / a.nbands);
-    const uint32_t y1 = 2u * (uint32_t)(((uint64_t)(band + 1) * (Y / 2)) / a.nbands);
+    // two tiers: ntall bands over rows [0, ytall), then the rest, shorter, over [ytall, Y); the
+    // short bands come later in launch order and fill the SM slots the tall ones free
+    const bool tall = band < a.ntall;
+    const uint32_t tb = tall ? band : band - a.ntall, tn = tall ? a.ntall : a.nbands - a.ntall;
+    const uint32_t ty = tall ? 0u : a.ytall, th = (tall ? a.ytall : Y - a.ytall) / 2;
+    const uint32_t y0 = ty + 2u * (uint32_t)(((uint64_t)tb * th) / tn);
+    const uint32_t y1 = ty + 2u * (uint32_t)(((uint64_t)(tb + 1) * th) / tn);
     // halo: 2K rows below, 2K + 2 above (the top row's sy- words need the row above it, and
     // the first streamed row stays even); rows are taken modulo Y, so a band taller than the
     // lattice streams some rows twice, as the periodic lattice unrolled along y

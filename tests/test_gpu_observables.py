@@ -6,6 +6,9 @@
   state that does not close is reported with SCA_ESTATE.
 * Edwards-Wilkinson growth for p = q (Sec. I.A): at L = 4096 the roughness grows
   logarithmically (about equal increments per factor of t) where q = 0 (KPZ) grows as a power.
+* A run's observations on the wavefront kernel with repeated times (no launch between two
+  observations) and gaps of several launches: exact sums at every time and the final state
+  against the oracle, and against the two-pass kernel from a rough surface at larger sizes.
 """
 import numpy as np
 import pytest
@@ -182,3 +185,48 @@ def test_origin_tracking_needs_a_surface(sca):
         assert e.value.code == sca.ESTATE
         sim.track_origin(False)
         sim.step(1)
+
+
+@pytest.mark.parametrize("L,p,q,times,k", [
+    (1024, 0.75, 0.25, [1, 1, 2, 6, 6, 7, 23, 24, 40], 4),
+    (1024, 1.0, 1.0, [3, 3, 16, 17, 49, 49, 80], 16),
+    (768, 0.7, 0.3, [1, 3, 3, 8, 13], 2),
+])
+def test_run_observations_against_oracle(sca, L, p, q, times, k):
+    """Every observation of a run equals the oracle's sums at its time, including a repeated
+    time (no launch between two observations) and gaps of several launches; the final state
+    too."""
+    seed = 17
+    with sca.Sim(L, seed=seed, p=p, q=q, kernel=sca.KERNEL_WAVE) as sim:
+        sim.set_temporal_block(k)
+        assert sim.kernel_in_use() == sca.KERNEL_WAVE
+        obs = sim.run(times)
+        words = sim.get_state()
+    bx, by = o.init_flat(L)
+    t = 0
+    for g, tt in zip(obs, times):
+        o.run(bx, by, seed, p, q, t0=t, n_mcs=tt - t)
+        t = tt
+        r = o.observe(bx, by)
+        assert (g.t, g.status, g.S1, g.S2, g.num) == (tt, 0, r["S1"], r["S2"], r["num"]), tt
+    assert np.array_equal(words, o.pack(bx, by))
+
+
+@pytest.mark.parametrize("L,p,q,times", [(8192, 1.0, 0.0, [16, 16, 17, 49, 50, 130]),
+                                         (16384, 0.5, 0.0, [4, 8, 8, 9, 28, 60])])
+def test_run_observations_large(sca, L, p, q, times):
+    """From a rough surface (3 MCS of p = 5/8, q = 3/8) at larger sizes: the run's observations
+    and final state on the wavefront kernel equal those of the two-pass kernel."""
+    import torch
+    with sca.Sim(L, seed=31, p=0.625, q=0.375, kernel=sca.KERNEL_TWO_PASS) as sim:
+        sim.step(3)
+        words = sim.get_state()
+    res = []
+    for kernel in (sca.KERNEL_WAVE, sca.KERNEL_TWO_PASS):
+        with sca.Sim(L, seed=5, p=p, q=q, kernel=kernel) as sim:
+            sim.set_state(words, t=0)
+            assert sim.kernel_in_use() == kernel
+            obs = sim.run(times)
+            res.append(([(g.t, g.status, g.S1, g.S2, g.num) for g in obs], sim.state_tensor().clone()))
+    assert res[0][0] == res[1][0]
+    assert torch.equal(res[0][1], res[1][1])

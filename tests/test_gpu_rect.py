@@ -115,6 +115,28 @@ def test_rect_wide_lattice_default_choice(sca):
     assert np.array_equal(words, words_o)
 
 
+def test_rect_tall_two_tier_plan_equals_two_pass(sca):
+    """A tall lattice (X = 4096, Y = 2^18: three column tiles, the last one ragged) from a rough
+    surface at 16 MCS per launch, where the wavefront's launch plan has a second tier of
+    shorter bands: the device state and exact sums equal those of the two-pass kernel."""
+    import torch
+    X, Y, times = 4096, 262144, [16, 40]
+    with sca.Sim(X, seed=31, p=0.625, q=0.375, Ly=Y, kernel=sca.KERNEL_TWO_PASS) as sim:
+        sim.step(3)
+        words = sim.get_state()
+    res = []
+    for kernel in (sca.KERNEL_WAVE, sca.KERNEL_TWO_PASS):
+        with sca.Sim(X, seed=5, p=1.0, q=0.0, Ly=Y, kernel=kernel) as sim:
+            sim.set_state(words, t=0)
+            if kernel == sca.KERNEL_WAVE:
+                sim.set_temporal_block(16)
+            assert sim.kernel_in_use() == kernel
+            obs = sim.run(times)
+            res.append(([(g.S1, g.S2, g.num) for g in obs], sim.state_tensor().clone()))
+    assert res[0][0] == res[1][0]
+    assert torch.equal(res[0][1], res[1][1])
+
+
 def test_rect_refusals_and_state_check(sca):
     """Kernels 2 and 3 refuse X != Y; a loaded state with one flipped slope is not a surface:
     the wavefront kernel refuses it, the two-pass kernel runs it, and the observation reports

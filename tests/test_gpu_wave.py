@@ -275,8 +275,10 @@ def _device_rows(sim, L, rows):
     return st.index_select(2, idx).cpu().numpy().view(np.uint32)
 
 
-@pytest.mark.parametrize("L,times,nrows,y_firsts", [(65536, [16, 40], 320, (1000, 65536 - 150)),
-                                                     (131072, [16, 33], 256, (131072 - 90,))])
+# windows: inside a band, across the periodic boundary in y, and across the boundary between
+# the launch plan's tall bands and its second tier of shorter ones (rows 58984 and 117966)
+@pytest.mark.parametrize("L,times,nrows,y_firsts", [(65536, [16, 40], 320, (1000, 65536 - 150, 58984 - 160)),
+                                                     (131072, [16, 33], 256, (131072 - 90, 117966 - 128))])
 def test_headline_kernel_rough_band_against_oracle(sca, L, times, nrows, y_firsts):
     """The benchmark's kernel (height bits, 16 MCS per launch, then the shorter launch up to the
     last time) at the benchmark's lattice and at the largest one, checked against the oracle
