@@ -34,9 +34,9 @@ __device__ __forceinline__ int64_t warp_sum(int64_t v)
 }
 
 // Table over the 256 values of (4 even-x bits, 4 odd-x bits): for the 8 sites in x order
-// (e0, o0, e1, o1, ...), slopes s = 2b - 1, running offsets d_k = s_0 + ... + s_k:
-// bits 0-7: sum s + 8 (<= 16), bits 8-17: sum d + 36 (<= 72), bits 18-28: sum d^2 (<= 204).
-// The fields are wide enough that eight entries add without carrying into each other.
+// (e0, o0, e1, o1, ...), slopes s = 2b - 1, running offsets d_k = s_0 + ... + s_k: byte 0 holds
+// S = d_7 + 8 (<= 16), bits 8-23 B = sum d_k^2 (<= 204, eight entries add to at most 1632),
+// byte 3 A = sum d_k + 36 (<= 72).
 __device__ __forceinline__ uint32_t nibble_pair_entry(uint32_t i)
 {
     int d = 0, sd = 0, sd2 = 0;
@@ -48,15 +48,18 @@ __device__ __forceinline__ uint32_t nibble_pair_entry(uint32_t i)
         sd += d;
         sd2 += d * d;
     }
-    return (uint32_t)(d + 8) | ((uint32_t)(sd + 36) << 8) | ((uint32_t)sd2 << 18);
+    return (uint32_t)(d + 8) | ((uint32_t)sd2 << 8) | ((uint32_t)(sd + 36) << 24);
 }
 
-// 32 sites of the even-x word e and the odd-x word o (x order e0, o0, e1, o1, ...), appended
-// to a chunk whose running offset is d: sd += sum of offsets, sd2 += sum of squared offsets.
-// With the 8-site blocks' entries (S_k, A_k, B_k) and dl_k the offset inside the pair before
-// block k, the pair adds 64 d + 8 sum dl + sum A to sd and
-// 64 d^2 + 16 d sum dl + 8 sum dl^2 + 2 d sum A + 2 sum dl A + sum B to sd2; the sums of the
-// entries come from one packed addition, only the dl terms need per-block work.
+// 64 sites of the even-x word e and the odd-x word o (x order e0, o0, e1, o1, ...), appended to
+// a chunk whose running offset is d: sd += sum of offsets, sd2 += sum of squared offsets.
+// Block k (8 sites) has the entry (S_k, A_k, B_k) and starts at offset d + dl_k inside the pair,
+// dl_k = S_0 + ... + S_{k-1}; the pair adds 64 d + X to sd and 64 d^2 + 2 d X + Z to sd2, with
+//   X = 8 sum dl_k + sum A_k,   Z = 8 sum dl_k^2 + 2 sum dl_k A_k + sum B_k.
+// The dl_k are formed four to a word as bytes, biased by 64 to lie in [8, 120]: the S bytes of
+// four blocks times 0x01010101 are their inclusive prefix sums, shifted up one byte the
+// exclusive ones; the sums over blocks are then byte dot products (dp4a), with the biases
+// taken out in closed form.  sum B_k comes from one sum of the entries (no field carries).
 // tab: the table replicated per lane, entry i of lane l at tab[32 i + l], so the 32 lanes of a
 // warp always read 32 different banks.
 __device__ __forceinline__ void obs_word_pair(const uint32_t *tab, uint32_t e, uint32_t o, int32_t &d,
@@ -65,26 +68,32 @@ __device__ __forceinline__ void obs_word_pair(const uint32_t *tab, uint32_t e, u
     // byte m of x0 indexes block 2m (nibble 2m of e and of o), byte m of x1 block 2m + 1
     const uint32_t x0 = (e & 0x0F0F0F0Fu) | ((o << 4) & 0xF0F0F0F0u);
     const uint32_t x1 = ((e >> 4) & 0x0F0F0F0Fu) | (o & 0xF0F0F0F0u);
-    uint32_t packed = 0;
-    int32_t dl = 0, sdl = 0, sdl2 = 0, sdla = 0;
+    uint32_t ent[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const uint32_t idx = ((k & 1) ? x1 : x0) >> (8 * (k >> 1)) & 0xFFu;
-        const uint32_t ent = tab[32u * idx];
-        packed += ent;
-        const int32_t A = (int32_t)((ent >> 8) & 1023u) - 36;
-        sdl += dl;
-        sdl2 += dl * dl;
-        sdla += dl * A;
-        dl += (int32_t)(ent & 255u) - 8;
-    }
-    const int32_t ST = (int32_t)(packed & 255u) - 64;
-    const int32_t SA = (int32_t)((packed >> 8) & 1023u) - 288;
-    const int32_t SB = (int32_t)(packed >> 18);
-    const int64_t D = d;
-    sd += 64 * d + 8 * sdl + SA;
-    sd2 += 64 * D * D + 16 * D * sdl + 8 * (int64_t)sdl2 + 2 * D * SA + 2 * (int64_t)sdla + SB;
-    d += ST;
+    for (int k = 0; k < 8; ++k)
+        ent[k] = tab[32u * __byte_perm((k & 1) ? x1 : x0, 0u, 0x4440u + (uint32_t)(k >> 1))];
+    uint32_t P = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) P += ent[k];
+    // S bytes (S0, S1) and A bytes (A0, A1) of blocks 0-3 and 4-7
+    const uint32_t l0 = __byte_perm(ent[0], ent[1], 0x7340u), h0 = __byte_perm(ent[2], ent[3], 0x7340u);
+    const uint32_t l1 = __byte_perm(ent[4], ent[5], 0x7340u), h1 = __byte_perm(ent[6], ent[7], 0x7340u);
+    const uint32_t S0 = __byte_perm(l0, h0, 0x5410u), A0 = __byte_perm(l0, h0, 0x7632u);
+    const uint32_t S1 = __byte_perm(l1, h1, 0x5410u), A1 = __byte_perm(l1, h1, 0x7632u);
+    const uint32_t I0 = S0 * 0x01010101u, I1 = S1 * 0x01010101u;   // inclusive sums of S + 8
+    // byte j: dl + 64 of block j (the constant 64 - 8 j takes out the S biases), of block 4 + j
+    const uint32_t D0 = (I0 << 8) + 0x28303840u;
+    const uint32_t D1 = (I1 << 8) + (I0 >> 24) * 0x01010101u + 0x08101820u;
+    const uint32_t q = __dp4a(D1, D1, __dp4a(D0, D0, 0u));   // sum (dl + 64)^2
+    const uint32_t r = __dp4a(D1, A1, __dp4a(D0, A0, 0u));   // sum (dl + 64)(A + 36)
+    const uint32_t u = __dp4a(D0 + D1, 0x01010101u, 0u);    // sum (dl + 64)
+    const uint32_t a = __dp4a(A0 + A1, 0x01010101u, 0u);    // sum (A + 36)
+    const int32_t SB = (int32_t)((P >> 8) & 0xFFFFu);
+    const int32_t X = 8 * (int32_t)u + (int32_t)a - 4384;
+    const int32_t Z = 8 * (int32_t)q + 2 * (int32_t)r - 1096 * (int32_t)u - 128 * (int32_t)a + 299008 + SB;
+    sd += 64 * d + X;
+    sd2 += (int64_t)d * (64 * d + 2 * X) + Z;
+    d += (int32_t)(I0 >> 24) + (int32_t)(I1 >> 24) - 64;
 }
 
 constexpr int kObsRowsWarps = 8;
@@ -109,18 +118,22 @@ template <bool VEC>
 __device__ void obs_rows_chunk(const uint32_t *A, uint32_t L, uint32_t Y, uint32_t r0, uint32_t r1,
                                ObsChunk *chunk)
 {
-    __shared__ uint32_t tabr[256 * 32];
+    __shared__ __align__(16) uint32_t tabr[256 * 32];
+    __shared__ uint32_t tab0[256];
     __shared__ int64_t sA[kObsChunkRows];
     __shared__ unsigned long long red2[kObsRowsWarps][2];
     __shared__ uint32_t sbits[kObsChunkRows / 32];
     __shared__ uint32_t red_flag;
-    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) {
-        const uint32_t v = nibble_pair_entry(i);
-#pragma unroll 8
-        for (int l = 0; l < 32; ++l) tabr[32 * i + l] = v;
-    }
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) tab0[i] = nibble_pair_entry(i);
     if (threadIdx.x < kObsChunkRows / 32) sbits[threadIdx.x] = 0;
     if (threadIdx.x == 0) red_flag = 0;
+    __syncthreads();
+    // the per-lane copies: consecutive threads write consecutive 16-byte groups (entry i fills
+    // words 32 i .. 32 i + 31), so the stores meet no bank conflict
+    for (uint32_t w = threadIdx.x; w < 256 * 8; w += blockDim.x) {
+        const uint32_t v = tab0[w >> 3];
+        reinterpret_cast<uint4 *>(tabr)[w] = make_uint4(v, v, v, v);
+    }
     __syncthreads();
     const uint32_t W = L / 64;                  // L: sites per row; Y: rows
     const size_t plane = (size_t)Y * W;
@@ -137,14 +150,22 @@ __device__ void obs_rows_chunk(const uint32_t *A, uint32_t L, uint32_t Y, uint32
         int32_t d = 0, sd = 0;
         int64_t sd2 = 0;
         if constexpr (VEC) {
-            // chunks of a lane are a multiple of 4 words: 16-byte loads, four word pairs at a time
+            // chunks of a lane are a multiple of 4 words (at least 4): 16-byte loads, four word
+            // pairs at a time, the next four loaded before these are reduced
+            uint4 e = *reinterpret_cast<const uint4 *>(pe + c0);
+            uint4 o = *reinterpret_cast<const uint4 *>(po + c0);
             for (uint32_t j = c0; j < c1; j += 4) {
-                const uint4 e = *reinterpret_cast<const uint4 *>(pe + j);
-                const uint4 o = *reinterpret_cast<const uint4 *>(po + j);
+                uint4 en = e, on = o;
+                if (j + 4 < c1) {
+                    en = *reinterpret_cast<const uint4 *>(pe + j + 4);
+                    on = *reinterpret_cast<const uint4 *>(po + j + 4);
+                }
                 obs_word_pair(tab, e.x, o.x, d, sd, sd2);
                 obs_word_pair(tab, e.y, o.y, d, sd, sd2);
                 obs_word_pair(tab, e.z, o.z, d, sd, sd2);
                 obs_word_pair(tab, e.w, o.w, d, sd, sd2);
+                e = en;
+                o = on;
             }
         } else {
             for (uint32_t j = c0; j < c1; ++j) obs_word_pair(tab, pe[j], po[j], d, sd, sd2);

@@ -143,10 +143,10 @@ def load(path: str = LIB_PATH):
 
 
 class ScaError(RuntimeError):
-    def __init__(self, code, where):
+    def __init__(self, code, where, detail=None):
         lib = load()
         msg = "%s: %s (%s)" % (where, lib.sca_strerror(code).decode(),
-                               lib.sca_last_error().decode())
+                               detail if detail is not None else lib.sca_last_error().decode())
         super().__init__(msg)
         self.code = code
 
@@ -251,7 +251,8 @@ class Sim:
         self.Ly = self.L if Ly is None else int(Ly)
         nbytes = workspace_bytes(self.L, self.Ly)
         if nbytes == 0:
-            raise ScaError(EINVAL, "L=%d Ly=%d" % (self.L, self.Ly))
+            raise ScaError(EINVAL, "L=%d Ly=%d" % (self.L, self.Ly),
+                           "L must be a multiple of 64 in [64, 131072] and Ly even in [2, 131072]")
         if workspace is None:
             workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         if workspace.numel() * workspace.element_size() < nbytes or not workspace.is_cuda:
