@@ -636,6 +636,22 @@ def run_ours(a, rank, world, local_rank):
         e2e_s = time.perf_counter() - t0
         sim2.close()
         e2e_value, e2e_s = aggregate_replicas(updates_per_step * a.steps, e2e_s, dist, dev)
+
+        # context, outside the timed regions: this host's pinned copy rate each way (one
+        # 1 GiB copy after a warm one, CUDA events on the simulation's stream)
+        def copy_GBs(dst, src):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                dst.copy_(src, non_blocking=True)
+                e0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return 4 * n_words / (e0.elapsed_time(e1) / 1e3) / 1e9
+        dev_buf = torch.empty(n_words, dtype=torch.int32, device=dev)
+        h2d_GBs, d2h_GBs = copy_GBs(dev_buf, host_in), copy_GBs(host_out, dev_buf)
+        del dev_buf
         obs_bytes = len(times) * sca.OBS_RECORD_BYTES
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 4 * n_words, "d2h_bytes_per_step": 4 * n_words + obs_bytes,
@@ -644,7 +660,8 @@ def run_ours(a, rank, world, local_rank):
                             "in), sca_run_async (after the other simulation's updates), "
                             "sca_get_state_async (1 GiB out), sca_wait",
                "sequential_value": seq_value,
-               "sequential_ms_per_step": 1000.0 * seq_s / a.steps}
+               "sequential_ms_per_step": 1000.0 * seq_s / a.steps,
+               "pinned_h2d_GBs": h2d_GBs, "pinned_d2h_GBs": d2h_GBs}
 
     # context: the paper's own benchmark case p = 1/2, q = 0 (random bits every update)
     extra = None
