@@ -675,15 +675,17 @@ int sca_wait(sca_sim *s, sca_obs *out, uint32_t n)
 {
     if (!s || (n && !out)) return fail(SCA_EINVAL, "NULL argument");
     if (n > s->async_obs) return fail(SCA_EINVAL, "more records than the last asynchronous run made");
-    cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "sca_wait");
+    // the records and the error word are read on the simulation's own stream, behind its work,
+    // so waiting never involves another stream's copies or kernels
     uint32_t err = 0;
-    e = cudaMemcpy(&err, s->err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && n) e = cudaMemcpy(out, s->res, n * sizeof(ObsDev), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpyAsync(&err, s->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess && n)
+        e = cudaMemcpyAsync(out, s->res, n * sizeof(ObsDev), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sca_wait");
     s->async_obs = 0;
     if (err) {
-        cudaMemset(s->err, 0, sizeof(uint32_t));
+        cudaMemsetAsync(s->err, 0, sizeof(uint32_t), s->stream);
         return fail(SCA_ETIMEOUT, "an update kernel's pipeline wait gave up; state invalid");
     }
     int first_bad = SCA_OK;
