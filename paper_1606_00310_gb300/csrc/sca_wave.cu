@@ -91,6 +91,7 @@ static bool wave_plan(uint32_t X, uint32_t Y, uint32_t k, int mode, uint32_t ban
 {
     if (X < 64 || X % 64 != 0 || Y < 2 || Y % 2 != 0 || k == 0 || (k & (k - 1)) != 0) return false;
     if ((int)k > wave_max_k(mode)) return false;
+    if ((uint64_t)Y * (X / 64) >= (1ull << 32)) return false;   // word indices are 32-bit
     const uint32_t W = X / 64, tw = kWaveTileWords * (uint32_t)wave_V(X, mode, k);
     const uint32_t nc = (W + tw - 1) / tw;
     uint32_t nb = bands;

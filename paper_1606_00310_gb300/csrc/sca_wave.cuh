@@ -321,10 +321,14 @@ __device__ __forceinline__ void wave_half_steps(const Rule &Rl, uint32_t (&h)[2 
         if constexpr (MODE == 1) {
             const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + Y - (uint32_t)i;
             const KeysRk key{Rl.rk};
+            // y W + j < 2^28 for every supported lattice (Y <= 2^17 rows, W <= 2^11 words, the
+            // plan refuses more): a 32-bit multiply-add, and the counter's high word parts are
+            // known to be zero (+4 % at p = 1/2 against the 64-bit product)
+            const uint64_t g = (uint64_t)(y * W + j);
             if constexpr (ND == 0)
-                wave_xi<V>(Rl, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
+                wave_xi<V>(Rl, key, g, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
             else
-                wave_xi_fixed<V, ND, DP, DQ>(Rl, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
+                wave_xi_fixed<V, ND, DP, DQ>(Rl, key, g, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) {

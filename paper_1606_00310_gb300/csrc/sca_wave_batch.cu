@@ -156,10 +156,11 @@ __global__ void __launch_bounds__(32 * kWBWarps) k_wave_batch(const WBArgs a)
                 uint32_t xp[V] = {}, xq[V] = {};
                 if constexpr (MODE == 1) {
                     const uint32_t y = yu >= (uint32_t)i ? yu - (uint32_t)i : yu + L - (uint32_t)i;
+                    // word index y W + j < 2^16 (L <= 2048): a 32-bit multiply-add
                     if constexpr (ND == 0)
-                        wave_xi<V>(a.R, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
+                        wave_xi<V>(a.R, key, (uint64_t)(y * W + j), t0 + (uint32_t)((i - 1) >> 1), s, xp, xq);
                     else
-                        wave_xi_fixed<V, ND, DP, DQ>(a.R, key, (uint64_t)y * W + j, t0 + (uint32_t)((i - 1) >> 1),
+                        wave_xi_fixed<V, ND, DP, DQ>(a.R, key, (uint64_t)(y * W + j), t0 + (uint32_t)((i - 1) >> 1),
                                                      s, xp, xq);
                 }
 #pragma unroll
