@@ -8,7 +8,7 @@ namespace sca {
 
 // Dyadic instantiations (other translation unit, compiled in parallel); V words per lane.
 cudaError_t launch_wave_dyadic(const WaveArgs &a, int K, int V, int grid, cudaStream_t st);
-int wave_dyadic_blocks_per_sm(const Rule &R, int K, int V);
+int wave_dyadic_blocks_per_sm(const Rule &R, int K, int V, uint32_t X, uint32_t Y);
 // Per-site uniform instantiations (sca_wave_uniform.cu), one word per lane.
 cudaError_t launch_wave_uniform(const WaveArgs &a, int K, int grid, cudaStream_t st);
 int wave_uniform_blocks_per_sm(int K);
@@ -69,9 +69,9 @@ uint32_t wave_pick_k(uint32_t want, int mode)
     return cap ? k : 0;
 }
 
-static int blocks_for(int K, int V, const Rule &R)
+static int blocks_for(int K, int V, const Rule &R, uint32_t X, uint32_t Y)
 {
-    if (R.mode == 1) return wave_dyadic_blocks_per_sm(R, K, V);
+    if (R.mode == 1) return wave_dyadic_blocks_per_sm(R, K, V, X, Y);
     if (R.mode == 2) return wave_uniform_blocks_per_sm(K);
     const bool dp = R.Pp != 0, dq = R.Pq != 0;
     switch (K) {
@@ -158,7 +158,7 @@ cudaError_t launch_wave_xy(const uint32_t *src, uint32_t *dst, uint32_t X, uint3
     uint32_t nb, nc;
     if (!wave_plan(X, Y, k, mode, bands, 1, &nb, &nc)) return cudaErrorInvalidValue;
     const int V = wave_V(X, mode, k);
-    if (!wave_plan(X, Y, k, mode, bands, blocks_for((int)k, V, R), &nb, &nc)) return cudaErrorInvalidValue;
+    if (!wave_plan(X, Y, k, mode, bands, blocks_for((int)k, V, R, X, Y), &nb, &nc)) return cudaErrorInvalidValue;
     uint32_t ntall = nb, ytall = Y;
     if (bands == 0) wave_tiers(Y, k, mode, &nb, &ntall, &ytall);
     const WaveArgs a{src, dst, X, X / 64, Y, nb, nc, ntall, ytall, t0, t_dev, R};

@@ -437,8 +437,10 @@ __device__ __forceinline__ void wave_block01(const Rule &Rl, WaveTile &T, uint32
 // window (2K+1+U slots) shifts by U slots per iteration.  MODE 0: p, q in {0, 1} with
 // DP = (p == 1), DQ = (q == 1); MODE 1: dyadic draws, ND of them fixed at compile time (0: the
 // rule's count at run time), DP / DQ = (p != 0) / (q != 0); MODE 2: per-site uniforms.
-template <int K, int V, int U, int MODE, bool DP, bool DQ, int ND = 0>
-__global__ void __launch_bounds__(32 * kWaveWarps, wave_min_blocks(K, V, MODE)) k_wave(const WaveArgs a)
+// MINB: resident CTAs per SM the compiler must allow (negative: the policy above).
+template <int K, int V, int U, int MODE, bool DP, bool DQ, int ND = 0, int MINB = -1>
+__global__ void __launch_bounds__(32 * kWaveWarps, MINB >= 0 ? MINB : wave_min_blocks(K, V, MODE))
+    k_wave(const WaveArgs a)
 {
     constexpr int S = 2 * K;                    // half-steps per launch
     constexpr int NW = S + 1 + U;               // row slots: slot of row R = R - R0 + S + 1

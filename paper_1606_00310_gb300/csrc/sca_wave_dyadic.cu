@@ -7,10 +7,10 @@
 
 namespace sca {
 
-template <int K, int V, bool DQ, int ND>
+template <int K, int V, bool DQ, int ND, int MINB = -1>
 static cudaError_t launch_one(const WaveArgs &a, int grid, cudaStream_t st, int *blocks)
 {
-    auto kern = k_wave<K, V, kWaveU1, 1, true, DQ, ND>;
+    auto kern = k_wave<K, V, kWaveU1, 1, true, DQ, ND, MINB>;
     if (blocks) {
         static int n = 0;
         if (n == 0) {
@@ -26,14 +26,22 @@ static cudaError_t launch_one(const WaveArgs &a, int grid, cudaStream_t st, int 
     return cudaGetLastError();
 }
 
+// The one-draw, q = 0 kernel at 4 MCS per launch is held to 128 registers (16 warps per SM
+// instead of 12) on lattices of 2^32 sites or more: +1.3 % at L = 65536 and +2.6 % at 131072,
+// but -2.5 % at 32768, where the plan then cuts more, shorter bands.
 template <int K>
 static cudaError_t dispatch_k(const WaveArgs &a, int V, int grid, cudaStream_t st, int *blocks)
 {
     const Rule &R = a.R;
     const bool dp = !(R.np == 0 && R.Pp == 0), dq = !(R.nq == 0 && R.Pq == 0);
     if (V == 4 && dp && R.n_draws >= 1 && R.n_draws <= 3) {
+        const bool large = (uint64_t)a.L * a.Y >= (1ull << 32);
         switch (R.n_draws * 2 + (dq ? 1 : 0)) {
-        case 2: return launch_one<K, 4, false, 1>(a, grid, st, blocks);
+        case 2:
+            if constexpr (K == 4) {
+                if (large) return launch_one<4, 4, false, 1, 16>(a, grid, st, blocks);
+            }
+            return launch_one<K, 4, false, 1>(a, grid, st, blocks);
         case 3: return launch_one<K, 4, true, 1>(a, grid, st, blocks);
         case 4: return launch_one<K, 4, false, 2>(a, grid, st, blocks);
         case 5: return launch_one<K, 4, true, 2>(a, grid, st, blocks);
@@ -55,10 +63,12 @@ static cudaError_t dispatch(const WaveArgs &a, int K, int V, int grid, cudaStrea
     }
 }
 
-int wave_dyadic_blocks_per_sm(const Rule &R, int K, int V)
+int wave_dyadic_blocks_per_sm(const Rule &R, int K, int V, uint32_t X, uint32_t Y)
 {
     WaveArgs a{};
     a.R = R;
+    a.L = X;
+    a.Y = Y;
     int b = 1;
     if (dispatch(a, K, V, 0, nullptr, &b) != cudaSuccess) return 1;
     return b;
