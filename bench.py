@@ -150,7 +150,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
@@ -161,13 +161,20 @@ class ClockSampler:
                 mx.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(parts[3]))
+            except ValueError:
+                pass
             for n, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+               "reasons": sorted(reasons), "samples": len(sm), "sm_mhz_min": min(sm)}
+        if pw:
+            out["power_w_median"] = statistics.median(pw)
+        return out
 
 
 # ----------------------------------------------------------------------------- roofline inputs
@@ -594,11 +601,13 @@ def run_ours(a, rank, world, local_rank):
         # one simulation, synchronous calls: copies and updates in sequence (context)
         e2e_step()
         sync_all()
+        clk_seq = ClockSampler(gpu_index)
         t0 = time.perf_counter()
         for _ in range(a.steps):
             e2e_step()
         sync_all()
         seq_s = time.perf_counter() - t0
+        clk_seq = clk_seq.stop()
         seq_value, seq_s = aggregate_replicas(updates_per_step * a.steps, seq_s, dist, dev)
 
         # two simulations on two streams, asynchronous calls: step i's host copies overlap
@@ -630,10 +639,19 @@ def run_ours(a, rank, world, local_rank):
 
         pipelined(2)
         sync_all()
+        sim.timing(True)
+        sim2.timing(True)
+        clk_e2e = ClockSampler(gpu_index)
         t0 = time.perf_counter()
         pipelined(a.steps)
         sync_all()
         e2e_s = time.perf_counter() - t0
+        clk_e2e = clk_e2e.stop()
+        # the updates' own device time inside the pipelined region (CUDA events around each
+        # run's update launches): the difference to ms_per_step is what the copies did not hide
+        e2e_upd_ms = sim.timing_read()[0] + sim2.timing_read()[0]
+        sim.timing(False)
+        sim2.timing(False)
         sim2.close()
         e2e_value, e2e_s = aggregate_replicas(updates_per_step * a.steps, e2e_s, dist, dev)
 
@@ -661,7 +679,9 @@ def run_ours(a, rank, world, local_rank):
                             "sca_get_state_async (1 GiB out), sca_wait",
                "sequential_value": seq_value,
                "sequential_ms_per_step": 1000.0 * seq_s / a.steps,
-               "pinned_h2d_GBs": h2d_GBs, "pinned_d2h_GBs": d2h_GBs}
+               "pinned_h2d_GBs": h2d_GBs, "pinned_d2h_GBs": d2h_GBs,
+               "update_ms_per_step": e2e_upd_ms / a.steps,
+               "clocks": clk_e2e, "clocks_sequential": clk_seq}
 
     # context: the paper's own benchmark case p = 1/2, q = 0 (random bits every update)
     extra = None
