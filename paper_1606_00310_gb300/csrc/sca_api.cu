@@ -401,6 +401,10 @@ int sca_get_kernel(const sca_sim *s)
     return effective_kernel(s, nullptr);
 }
 
+#ifndef SCA_WAVE_SX_SKIP
+#define SCA_WAVE_SX_SKIP 1
+#endif
+
 int sca::step_impl(sca_sim *s, uint64_t n)
 {
     if (n == 0) return SCA_OK;
@@ -441,6 +445,14 @@ int sca::step_impl(sca_sim *s, uint64_t n)
         while (done < n) {
             const uint64_t k = (n - done) < (uint64_t)tbk ? (n - done) : (uint64_t)tbk;
             const uint64_t kk = kern == 3 ? k : wave_pick_k((uint32_t)k, (int)s->R.mode);
+            // a wavefront launch followed by one of the same plan leaves the sx- planes to it,
+            // except the rows that launch starts its bands from; the last one writes them all
+            bool sx_all = true;
+            if (SCA_WAVE_SX_SKIP && kern == 4 && !s->track_origin) {
+                const uint64_t rest = n - done - kk;
+                const uint64_t k2 = rest < (uint64_t)tbk ? rest : (uint64_t)tbk;
+                sx_all = rest == 0 || wave_pick_k((uint32_t)k2, (int)s->R.mode) != kk;
+            }
             if (s->track_origin) {           // the launch's MCS re-run around the origin first
                 cudaError_t e = launch_origin_track(s->buf[s->cur], s->L, s->Ly, s->t + done,
                                                     (uint32_t)(kern == 3 ? k : kk), s->R, s->h00, s->stream);
@@ -450,7 +462,7 @@ int sca::step_impl(sca_sim *s, uint64_t n)
                 ? launch_tblock(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->t + done, (uint32_t)k,
                                 s->R, s->stream)
                 : launch_wave_xy(s->buf[s->cur], s->buf[s->cur ^ 1], s->L, s->Ly, s->t + done, (uint32_t)kk,
-                                 s->R, s->stream, nullptr, s->wave_bands);
+                                 s->R, s->stream, nullptr, s->wave_bands, sx_all);
             if (e != cudaSuccess) {
                 s->t += done;
                 return cuda_fail(e, "temporal-blocking launch");

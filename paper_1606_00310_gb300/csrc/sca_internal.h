@@ -65,10 +65,12 @@ bool tblock_plan(uint32_t L, uint32_t k, uint32_t *nslabs, size_t *smem);
 cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t t0, uint32_t k,
                         const Rule &R, cudaStream_t st, const uint64_t *t_dev = nullptr,
                         uint32_t bands = 0);
-// The same on an X x Y lattice (X sites per row, Y rows).
+// The same on an X x Y lattice (X sites per row, Y rows).  sx_all false: the output's sx-
+// planes are written only on the rows the next launch of the same plan (same k and bands)
+// integrates its first rows from; the output is then a valid state only for such a launch.
 cudaError_t launch_wave_xy(const uint32_t *src, uint32_t *dst, uint32_t X, uint32_t Y, uint64_t t0, uint32_t k,
                            const Rule &R, cudaStream_t st, const uint64_t *t_dev = nullptr,
-                           uint32_t bands = 0);
+                           uint32_t bands = 0, bool sx_all = true);
 bool wave_supported(uint32_t L, uint32_t k, int mode);
 bool wave_supported_xy(uint32_t X, uint32_t Y, uint32_t k, int mode);
 int wave_max_k(int mode);

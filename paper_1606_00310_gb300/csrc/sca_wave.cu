@@ -152,7 +152,7 @@ cudaError_t launch_wave(const uint32_t *src, uint32_t *dst, uint32_t L, uint64_t
 }
 
 cudaError_t launch_wave_xy(const uint32_t *src, uint32_t *dst, uint32_t X, uint32_t Y, uint64_t t0, uint32_t k,
-                           const Rule &R, cudaStream_t st, const uint64_t *t_dev, uint32_t bands)
+                           const Rule &R, cudaStream_t st, const uint64_t *t_dev, uint32_t bands, bool sx_all)
 {
     const int mode = (int)R.mode;
     uint32_t nb, nc;
@@ -161,7 +161,11 @@ cudaError_t launch_wave_xy(const uint32_t *src, uint32_t *dst, uint32_t X, uint3
     if (!wave_plan(X, Y, k, mode, bands, blocks_for((int)k, V, R, X, Y), &nb, &nc)) return cudaErrorInvalidValue;
     uint32_t ntall = nb, ytall = Y;
     if (bands == 0) wave_tiers(Y, k, mode, &nb, &ntall, &ytall);
-    const WaveArgs a{src, dst, X, X / 64, Y, nb, nc, ntall, ytall, t0, t_dev, R};
+    // the row a band keeps sx- words for must be one of its final rows: bands of at least
+    // 2k + 2 rows (the planner's are at least 8k; an explicit band count may cut shorter ones)
+    if (2u * (ytall / 2 / ntall) < 2u * k + 2u) sx_all = true;
+    if (nb > ntall && 2u * ((Y - ytall) / 2 / (nb - ntall)) < 2u * k + 2u) sx_all = true;
+    const WaveArgs a{src, dst, X, X / 64, Y, nb, nc, ntall, ytall, sx_all ? 1u : 0u, t0, t_dev, R};
     const uint64_t tiles = (uint64_t)nb * nc;
     const int grid = (int)((tiles + kWaveWarps - 1) / kWaveWarps);
     count_launches(1);

@@ -40,6 +40,7 @@ struct WaveArgs {
     uint32_t Y;              // rows
     uint32_t nbands, ncols;  // tiles: bands of rows x columns of words
     uint32_t ntall, ytall;   // the first ntall bands share rows [0, ytall), the rest [ytall, Y)
+    uint32_t sx_all;         // 0: sx- planes only on each band's row y1 - 2K - 2 (see below)
     uint64_t t0;             // MCS index of the first step, or offset from *t_dev
     const uint64_t *t_dev;
     Rule R;
@@ -341,18 +342,28 @@ __device__ __forceinline__ void wave_half_steps(const Rule &Rl, uint32_t (&h)[2 
 // word offset o: sy-bit = b xor b(x, y-1) xor s and sx-bit = b xor b(x-1, y) xor s.  In even
 // rows sublattice 0 sits at even x, so its left neighbour is bit k-1 of the sublattice-1 word
 // and sublattice 1's is bit k of the sublattice-0 word; odd rows (odd u) the other way round.
+// with_sx false (warp-uniform): the sy- words only.
 template <int V>
 __device__ __forceinline__ void wave_store_row(const uint32_t (&hr)[2][V], const uint32_t (&hp)[2][V], const int u,
-                                               const bool own, const uint32_t o, uint32_t *DX0, uint32_t *DY0,
-                                               uint32_t *DX1, uint32_t *DY1)
+                                               const bool own, const bool with_sx, const uint32_t o, uint32_t *DX0,
+                                               uint32_t *DY0, uint32_t *DX1, uint32_t *DY1)
 {
-    const int lo = (u & 1) ? 1 : 0;             // sublattice whose left neighbour is shifted
-    const uint32_t pv = __shfl_up_sync(0xFFFFFFFFu, hr[lo ^ 1][V - 1], 1);
-    uint32_t sx[2][V], sy[2][V];
+    uint32_t sy[2][V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         sy[0][v] = hr[0][v] ^ hp[1][v];
         sy[1][v] = ~(hr[1][v] ^ hp[0][v]);
+    }
+    if (own) {
+        wave_st<V>(DY0 + o, sy[0]);
+        wave_st<V>(DY1 + o, sy[1]);
+    }
+    if (!with_sx) return;
+    const int lo = (u & 1) ? 1 : 0;             // sublattice whose left neighbour is shifted
+    const uint32_t pv = __shfl_up_sync(0xFFFFFFFFu, hr[lo ^ 1][V - 1], 1);
+    uint32_t sx[2][V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
         const uint32_t left = __funnelshift_l(v ? hr[lo ^ 1][(v + V - 1) % V] : pv, hr[lo ^ 1][v], 1);
         sx[lo][v] = hr[lo][v] ^ left;
         sx[lo ^ 1][v] = hr[lo ^ 1][v] ^ hr[lo][v];
@@ -361,9 +372,7 @@ __device__ __forceinline__ void wave_store_row(const uint32_t (&hr)[2][V], const
     for (int v = 0; v < V; ++v) sx[1][v] = ~sx[1][v];
     if (own) {
         wave_st<V>(DX0 + o, sx[0]);
-        wave_st<V>(DY0 + o, sy[0]);
         wave_st<V>(DX1 + o, sx[1]);
-        wave_st<V>(DY1 + o, sy[1]);
     }
 }
 
@@ -400,6 +409,8 @@ struct WaveTile {
     uint32_t L, W, plane, NR, j;
     uint32_t ol;     // word offset of the next row to load (32 bits: a plane holds <= 2^28 words)
     uint32_t os;     // word offset of the next final row to store
+    uint32_t rsx;    // the one row R whose sx- words are stored (all rows: sx_all)
+    bool sx_all;
     bool own;        // this lane stores its words
 };
 
@@ -426,7 +437,8 @@ __device__ __forceinline__ void wave_block01(const Rule &Rl, WaveTile &T, uint32
         if (T.ol >= T.plane) T.ol -= T.plane;
         wave_half_steps<K, V, U, 0, DP, DQ, 0>(Rl, h, u, 0u, T.L, T.L, T.W, T.j, 0u);
         if (!CHK || R >= 4u * K + 2u) {         // row R - 2K is final
-            wave_store_row<V>(h[base + u - S], h[base + u - S - 1], u, T.own, T.os, T.DX0, T.DY0, T.DX1, T.DY1);
+            wave_store_row<V>(h[base + u - S], h[base + u - S - 1], u, T.own, T.sx_all || R == T.rsx, T.os, T.DX0,
+                              T.DY0, T.DX1, T.DY1);
             T.os += T.W;
         }
     }
@@ -530,6 +542,12 @@ __global__ void __launch_bounds__(32 * kWaveWarps, MINB >= 0 ? MINB : wave_min_b
         if (ol >= plane32) ol -= plane32;
     }
     uint32_t os = y0 * W + j;                   // lattice row y0 is the first final row
+    // The next launch of the same plan integrates band b's first row, y0(b) - 2K - 2, from its
+    // sx- words; that row is this band's row y1 - 2K - 2 (the next band starts at y1, the first
+    // at y1 = Y modulo Y), stored when R = y1 - y0 + 2K.  Every other row's sx- words can wait
+    // for the last launch before the state is read (sx_all).
+    const bool sx_all = a.sx_all != 0;
+    const uint32_t rsx = y1 - y0 + 2u * K;
     constexpr int base = S + 1;                 // slot of the first row of a block
 
     if constexpr (MODE == 0) {
@@ -538,6 +556,7 @@ __global__ void __launch_bounds__(32 * kWaveWarps, MINB >= 0 ? MINB : wave_min_b
         T.DX0 = DX0; T.DY0 = DY0; T.DX1 = DX1; T.DY1 = DY1;
         T.L = L; T.W = W; T.plane = plane32; T.NR = NR; T.j = j;
         T.ol = ol; T.os = os; T.own = own;
+        T.rsx = rsx; T.sx_all = sx_all;
         for (uint32_t R0 = 0; R0 < NR; R0 += U) {
             if (R0 >= 4u * K + 2u && R0 + U + P <= NR)
                 wave_block01<K, V, U, P, DP, DQ, false>(a.R, T, h, rc, R0);
@@ -561,7 +580,8 @@ __global__ void __launch_bounds__(32 * kWaveWarps, MINB >= 0 ? MINB : wave_min_b
                 if (ol >= plane32) ol -= plane32;
                 wave_half_steps<K, V, U, MODE, DP, DQ, ND>(a.R, h, u, yu, L, Y, W, j, t0);
                 if (R >= 4u * K + 2u) {         // row R - 2K is final
-                    wave_store_row<V>(h[base + u - S], h[base + u - S - 1], u, own, os, DX0, DY0, DX1, DY1);
+                    wave_store_row<V>(h[base + u - S], h[base + u - S - 1], u, own, sx_all || R == rsx, os, DX0,
+                                      DY0, DX1, DY1);
                     os += W;
                 }
                 if (++yu == Y) yu = 0;

@@ -120,7 +120,7 @@ def test_rect_tall_two_tier_plan_equals_two_pass(sca):
     surface at 16 MCS per launch, where the wavefront's launch plan has a second tier of
     shorter bands: the device state and exact sums equal those of the two-pass kernel."""
     import torch
-    X, Y, times = 10240, 131072, [16, 40]
+    X, Y, times = 10240, 131072, [48, 96]
     with sca.Sim(X, seed=31, p=0.625, q=0.375, Ly=Y, kernel=sca.KERNEL_TWO_PASS) as sim:
         sim.step(3)
         words = sim.get_state()

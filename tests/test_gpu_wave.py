@@ -224,6 +224,8 @@ def test_wave01_rough_against_oracle(sca, L, p, q, times, k):
     (4096, 1.0, 0.0, [40, 200], 16, None), (8192, 0.0, 1.0, [64, 96], 16, None),
     (6144, 1.0, 1.0, [35, 99], 16, None), (16384, 1.0, 0.0, [32, 160], None, None),
     (4096, 1.0, 0.0, [80], 16, 31), (2048, 1.0, 0.0, [96], 16, 2), (1984, 1.0, 0.0, [64], 16, None),
+    # bands of 32 rows, under 2K + 2: every launch writes its whole state
+    (2048, 1.0, 0.0, [48], 16, 64),
     (8192, 1.0, 0.0, [24, 88], 8, 5),
     # four words per lane (1 and 2 MCS per launch): several tiles, uneven bands
     (8192, 1.0, 0.0, [10, 31], 2, None), (4096, 0.0, 1.0, [9], 1, 7), (6144, 1.0, 1.0, [5, 12], 2, 3)])
@@ -277,11 +279,13 @@ def _device_rows(sim, L, rows):
 
 # windows: inside a band, across the periodic boundary in y, and across the boundary between
 # the launch plan's tall bands and its second tier of shorter ones (rows 58984 and 117966)
-@pytest.mark.parametrize("L,times,nrows,y_firsts", [(65536, [16, 40], 320, (1000, 65536 - 150, 58984 - 160)),
-                                                     (131072, [16, 33], 256, (131072 - 90, 117966 - 128))])
+@pytest.mark.parametrize("L,times,nrows,y_firsts", [(65536, [32, 40], 320, (1000, 65536 - 150, 58984 - 160)),
+                                                     (131072, [32, 33], 256, (131072 - 90, 117966 - 128))])
 def test_headline_kernel_rough_band_against_oracle(sca, L, times, nrows, y_firsts):
-    """The benchmark's kernel (height bits, 16 MCS per launch, then the shorter launch up to the
-    last time) at the benchmark's lattice and at the largest one, checked against the oracle
+    """The benchmark's kernel (height bits, two 16-MCS launches, the first leaving the sx- planes
+    to the second except on the rows the second starts its bands from, then the shorter launch
+    up to the last time) at the benchmark's lattice and at the largest one, checked against the
+    oracle
     itself on bands of rows, one of them wrapping around the periodic boundary in y.  Start: a
     rough surface, 3 MCS of p = 5/8, q = 3/8 (seed 31) from flat, made on the GPU by the two-pass
     kernel and by the band oracle from its own flat band (their common rows are compared too);
