@@ -408,7 +408,14 @@ static int wb_enqueue(sca_batch *b, uint32_t n)
             while (t < T && e == cudaSuccess) {
                 uint32_t k = 1;
                 while (2 * k <= kmax && 2 * k <= T - t) k *= 2;
-                e = launch_wave_batch(buf[cur], buf[cur ^ 1], c.items, c.n_items, c.L, c.rows, t, k, c.R, c.st);
+                // a launch followed by one of the same k before the observation leaves it the
+                // sx- planes but for the rows it starts its bands from
+                const uint64_t rest = T - t - k;
+                uint32_t k2 = 1;
+                while (2 * k2 <= kmax && 2 * k2 <= rest) k2 *= 2;
+                const bool sx_all = rest == 0 || k2 != k;
+                e = launch_wave_batch(buf[cur], buf[cur ^ 1], c.items, c.n_items, c.L, c.rows, t, k, c.R, c.st,
+                                      sx_all);
                 cur ^= 1;
                 t += k;
             }

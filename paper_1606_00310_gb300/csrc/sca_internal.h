@@ -98,7 +98,7 @@ bool wave_batch_supported(uint32_t L, const Rule &R);
 int wave_batch_max_k(const Rule &R);
 cudaError_t launch_wave_batch(const uint32_t *src, uint32_t *dst, const WBItem *items, uint32_t n_items,
                               uint32_t L, uint32_t rows_per_band, uint64_t t0, uint32_t k, const Rule &R,
-                              cudaStream_t st);
+                              cudaStream_t st, bool sx_all = true);
 cudaError_t launch_wave_batch_copy(const uint32_t *src, uint32_t *dst, const WBItem *items, uint32_t n_items,
                                    uint32_t L, cudaStream_t st);
 // Batched observation of n_lat lattices of size L (first words at base + off[i]); record of

@@ -21,6 +21,8 @@ struct WBArgs {
     uint32_t L, W, n;   // class lattice size, words per row, rows per band (even)
     uint32_t G;         // lanes per row group (W / V, a power of two <= 32)
     uint64_t t0;
+    uint32_t sx_all;    // 0: sx- words only on each band's row y0 + n - 2K - 2 (the row the next
+                        // launch of the same K starts the following band from)
     Rule R;             // class rule; the keys come from the items
 };
 
@@ -171,25 +173,34 @@ __global__ void __launch_bounds__(32 * kWBWarps) k_wave_batch(const WBArgs a)
                 const uint32_t(&hr)[2][V] = h[base + u - S];
                 const uint32_t(&hp)[2][V] = h[base + u - S - 1];
                 const uint32_t y = y0 + R - 4u * K - 2u;
-                const int lo = (u & 1) ? 1 : 0;
-                const uint32_t pv = __shfl_sync(FULL, hr[lo ^ 1][V - 1], lig + G - 1, G);
-                uint32_t sx[2][V], sy[2][V];
+                const size_t o = (size_t)y * W + j;
+                uint32_t sy[2][V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     sy[0][v] = hr[0][v] ^ hp[1][v];
                     sy[1][v] = ~(hr[1][v] ^ hp[0][v]);
-                    const uint32_t left = __funnelshift_l(v ? hr[lo ^ 1][(v + V - 1) % V] : pv, hr[lo ^ 1][v], 1);
-                    sx[lo][v] = hr[lo][v] ^ left;
-                    sx[lo ^ 1][v] = hr[lo ^ 1][v] ^ hr[lo][v];
                 }
-#pragma unroll
-                for (int v = 0; v < V; ++v) sx[1][v] = ~sx[1][v];
                 if (act) {
-                    const size_t o = (size_t)y * W + j;
-                    wave_st<V>(DX0 + o, sx[0]);
                     wave_st<V>(DY0 + o, sy[0]);
-                    wave_st<V>(DX1 + o, sx[1]);
                     wave_st<V>(DY1 + o, sy[1]);
+                }
+                // every group of the warp is at the same R: the branch is warp-uniform
+                if (a.sx_all || R == a.n + 2u * K) {
+                    const int lo = (u & 1) ? 1 : 0;
+                    const uint32_t pv = __shfl_sync(FULL, hr[lo ^ 1][V - 1], lig + G - 1, G);
+                    uint32_t sx[2][V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const uint32_t left = __funnelshift_l(v ? hr[lo ^ 1][(v + V - 1) % V] : pv, hr[lo ^ 1][v], 1);
+                        sx[lo][v] = hr[lo][v] ^ left;
+                        sx[lo ^ 1][v] = hr[lo ^ 1][v] ^ hr[lo][v];
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; ++v) sx[1][v] = ~sx[1][v];
+                    if (act) {
+                        wave_st<V>(DX0 + o, sx[0]);
+                        wave_st<V>(DX1 + o, sx[1]);
+                    }
                 }
             }
             if (++yu == L) yu = 0;
@@ -290,10 +301,11 @@ bool wave_batch_supported(uint32_t L, const Rule &R)
 
 cudaError_t launch_wave_batch(const uint32_t *src, uint32_t *dst, const WBItem *items, uint32_t n_items,
                               uint32_t L, uint32_t rows_per_band, uint64_t t0, uint32_t k, const Rule &R,
-                              cudaStream_t st)
+                              cudaStream_t st, bool sx_all)
 {
     const int V = wave_batch_V(L, R);
-    WBArgs a{src, dst, items, n_items, L, L / 64, rows_per_band, (L / 64) / (uint32_t)V, t0, R};
+    if (rows_per_band < 2 * k + 2) sx_all = true;     // the kept row must be one of the band's
+    WBArgs a{src, dst, items, n_items, L, L / 64, rows_per_band, (L / 64) / (uint32_t)V, t0, sx_all ? 1u : 0u, R};
     if (R.mode == 0) {
         switch (k) {
         case 1: return wb_mode0<1>(a, st);
