@@ -10,12 +10,12 @@
 
 namespace sca {
 
-// Launch shape of a "row team": T threads own W words of one sublattice row, V words each,
-// padded to TP threads so teams never straddle a warp in a way the scans cannot handle.
+// Launch shape of a "row team": T threads own W words of one sublattice row, V words each;
+// a team's threads share only the block's shared memory, so teams sit back to back.
 struct TeamShape {
     int V;          // words per thread per row (1, 2 or 4)
     int T;          // threads that own words
-    int TP;         // padded team size (power of two <= 32, or a multiple of 32)
+    int TP;         // threads per team (= T; teams are packed back to back)
     int teams;      // teams per block
     int block;      // threads per block = teams * TP
 };

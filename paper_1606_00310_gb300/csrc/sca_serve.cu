@@ -210,6 +210,15 @@ static int start(sca_server *srv, ServeReq *r)
     r->t_dev = reinterpret_cast<uint64_t *>(static_cast<char *>(r->mem) + ((ws + 255) & ~(size_t)255));
     int rc = sca_init(&r->P, sl.stream, r->mem, ws, &r->sim);
     if (rc) return rc;
+    // Requests share the GPU, so a request takes the kernel with the most throughput per SM,
+    // not the one that finishes a lattice alone soonest: per-site uniforms run the two-pass
+    // kernel at every size.  Temporal blocking plans one large-shared-memory CTA per SM even
+    // for a small lattice, so its launches cannot share the SMs with other requests' work, and
+    // its recomputed halos repeat Philox calls.
+    if (r->sim->R.mode == 2) {
+        rc = sca_set_kernel(r->sim, 1);
+        if (rc) return rc;
+    }
     return SCA_OK;
 }
 

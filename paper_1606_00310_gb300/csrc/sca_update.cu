@@ -46,7 +46,7 @@ struct HalfArgs {
     const uint64_t *t_dev;
     int s;
     int T;       // threads owning words in a team
-    int TP;      // padded team size
+    int TP;      // threads per team (= T)
     Rule R;
 };
 
@@ -152,13 +152,10 @@ static TeamShape team_shape_v(uint32_t W, int V, int max_block)
     TeamShape ts;
     ts.V = V;
     ts.T = (int)(W / ts.V);
-    if (ts.T <= 32) {
-        int p = 1;
-        while (p < ts.T) p <<= 1;
-        ts.TP = p;
-    } else {
-        ts.TP = (ts.T + 31) / 32 * 32;
-    }
+    // teams packed back to back: the kernel couples a team's threads through shared memory
+    // and block barriers only, so a warp may span two teams, and no lane idles for padding
+    // (rows of W = 100 words, say, would leave 7 of every 32 lanes idle in power-of-two teams)
+    ts.TP = ts.T;
     ts.teams = ts.TP >= max_block ? 1 : max_block / ts.TP;
     ts.block = ts.teams * ts.TP;
     return ts;

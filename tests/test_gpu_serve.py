@@ -172,9 +172,9 @@ def test_submit_state_refuses_a_short_buffer(sca):
 
 
 def test_served_kernels_agree(sca):
-    """Requests whose lattice runs with temporal blocking (small L), the two-pass kernel (per-site
-    uniforms at L = 4096) and the fused kernel (dyadic, L = 32768) all equal a single simulation
-    with the kernel fixed to two-pass."""
+    """Requests whose lattice runs with temporal blocking (dyadic, small L), the two-pass kernel
+    (per-site uniforms, which the server runs on it at every size) and the fused kernel (dyadic,
+    L = 32768) all equal a single simulation with the kernel fixed to two-pass."""
     reqs = [dict(L=512, p=0.75, q=0.25, seed=3, n=200), dict(L=1024, p=0.7, q=0.3, seed=4, n=130),
             dict(L=4096, p=0.6, q=0.4, seed=5, n=66), dict(L=32768, p=0.5, q=0.0, seed=6, n=66)]
     with sca.Server(budget_bytes=8 << 30, max_active=4, max_L=32768) as srv:
