@@ -6,7 +6,8 @@
 // state; admitted requests get stream-ordered memory from a pool, so admission never
 // synchronises the device.  Every active request keeps at most one piece of work in flight on
 // its own stream, so pieces of different requests overlap on the GPU, and a request that
-// arrives while others run starts as soon as a slot and memory free up.  Steps run as a
+// arrives while others run starts as soon as a slot and memory free up.  Short requests run on
+// a high-priority stream, so their blocks go first when the GPU is shared.  Steps run as a
 // captured CUDA graph of kChunk MCS, replayed with a device-resident MCS counter (the update
 // kernels read t from it), so the host issues one graph launch per kChunk MCS instead of one
 // or two kernel launches per MCS.  Each request's dynamics are exactly those of a single
@@ -29,6 +30,11 @@ namespace sca {
 
 constexpr uint32_t kChunk = 64;        // MCS per replayed graph (even: fused buffers return)
 constexpr uint32_t kChunksPerPiece = 4;
+// Requests of at most this many site updates (L^2 x MCS; about 8 ms of GPU work) run on their
+// slot's high-priority stream: when SM slots free up, the GPU's block scheduler starts their
+// blocks before those of larger requests, so short requests are not held behind long ones
+// (shortest-first on the device; admission stays in arrival order).
+constexpr uint64_t kShortWork = 1ull << 33;
 
 static uint64_t now_ns()
 {
@@ -50,6 +56,7 @@ struct ServeReq {
     std::vector<sca_obs> obs;
     uint32_t *final_words = nullptr;    // caller-owned host buffer for the final state (or null)
     // scheduler-owned while active
+    cudaStream_t st = nullptr;          // the slot's stream this request runs on
     void *mem = nullptr;
     sca_sim *sim = nullptr;
     uint64_t *t_dev = nullptr;
@@ -60,7 +67,8 @@ struct ServeReq {
 };
 
 struct Slot {
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;      // default priority
+    cudaStream_t stream_hi = nullptr;   // highest priority (short requests)
     cudaEvent_t ev = nullptr;
     sca_obs *pinned = nullptr;          // kResCap records
     bool busy = false;
@@ -156,7 +164,7 @@ static void release_gpu(sca_server *srv, ServeReq *r)
 {
     Slot &sl = srv->slots[r->slot];
     if (r->sim) {
-        sca_free(r->sim);            // synchronises the slot stream; memory is the pool's
+        sca_free(r->sim);            // synchronises the request's stream; memory is the pool's
         r->sim = nullptr;
     }
     for (int p = 0; p < 2; ++p)
@@ -165,7 +173,7 @@ static void release_gpu(sca_server *srv, ServeReq *r)
             r->chunk[p] = nullptr;
         }
     if (r->mem) {
-        cudaFreeAsync(r->mem, sl.stream);
+        cudaFreeAsync(r->mem, r->st);
         r->mem = nullptr;
     }
 }
@@ -204,11 +212,12 @@ static void finish(sca_server *srv, ServeReq *r, int status)
 static int start(sca_server *srv, ServeReq *r)
 {
     Slot &sl = srv->slots[r->slot];
-    cudaError_t e = cudaMallocFromPoolAsync(&r->mem, r->need + 256, srv->pool, sl.stream);
+    r->st = (uint64_t)r->P.L * r->P.L * r->n_mcs <= kShortWork ? sl.stream_hi : sl.stream;
+    cudaError_t e = cudaMallocFromPoolAsync(&r->mem, r->need + 256, srv->pool, r->st);
     if (e != cudaSuccess) return fail(SCA_ENOMEM, "pool allocation");
     const size_t ws = sca_workspace_bytes(r->P.L);
     r->t_dev = reinterpret_cast<uint64_t *>(static_cast<char *>(r->mem) + ((ws + 255) & ~(size_t)255));
-    int rc = sca_init(&r->P, sl.stream, r->mem, ws, &r->sim);
+    int rc = sca_init(&r->P, r->st, r->mem, ws, &r->sim);
     if (rc) return rc;
     // Requests share the GPU, so a request takes the kernel with the most throughput per SM,
     // not the one that finishes a lattice alone soonest: per-site uniforms run the two-pass
@@ -230,33 +239,33 @@ static int enqueue_piece(sca_server *srv, ServeReq *r)
     const uint32_t n = (uint32_t)r->times.size();
     while (r->next_obs < n && r->times[r->next_obs] == s->t) {
         cudaError_t e = launch_observe(s->buf[s->cur], s->L, s->h0, s->part, s->res + r->next_obs,
-                                       s->t, sl.stream);
+                                       s->t, r->st);
         if (e != cudaSuccess) return cuda_fail(e, "observe launch");
         r->next_obs++;
     }
     if (r->next_obs == n) {
-        cudaError_t e = cudaMemcpyAsync(sl.pinned, s->res, n * sizeof(sca_obs), cudaMemcpyDeviceToHost, sl.stream);
+        cudaError_t e = cudaMemcpyAsync(sl.pinned, s->res, n * sizeof(sca_obs), cudaMemcpyDeviceToHost, r->st);
         if (e != cudaSuccess) return cuda_fail(e, "result copy");
         if (r->final_words) {
             e = cudaMemcpyAsync(r->final_words, s->buf[s->cur], s->lo.state_bytes, cudaMemcpyDeviceToHost,
-                                sl.stream);
+                                r->st);
             if (e != cudaSuccess) return cuda_fail(e, "final state copy");
         }
         r->copying = true;
     } else {
         const uint64_t gap = r->times[r->next_obs] - s->t;
         if (gap >= kChunk) {
-            cudaError_t e = capture_chunk(r, sl.stream);
+            cudaError_t e = capture_chunk(r, r->st);
             if (e != cudaSuccess) return cuda_fail(e, "step graph");
             if (!r->t_dev_synced) {
-                e = launch_set_t(r->t_dev, s->t, sl.stream);
+                e = launch_set_t(r->t_dev, s->t, r->st);
                 if (e != cudaSuccess) return cuda_fail(e, "counter");
                 r->t_dev_synced = true;
             }
             uint64_t k = gap / kChunk;
             if (k > kChunksPerPiece) k = kChunksPerPiece;
             for (uint64_t c = 0; c < k; ++c) {
-                e = cudaGraphLaunch(r->chunk[s->cur], sl.stream);
+                e = cudaGraphLaunch(r->chunk[s->cur], r->st);
                 if (e != cudaSuccess) return cuda_fail(e, "graph launch");
                 {
                     int tk = 0;
@@ -279,7 +288,7 @@ static int enqueue_piece(sca_server *srv, ServeReq *r)
             r->t_dev_synced = false;
         }
     }
-    cudaError_t e = cudaEventRecord(sl.ev, sl.stream);
+    cudaError_t e = cudaEventRecord(sl.ev, r->st);
     if (e != cudaSuccess) return cuda_fail(e, "event");
     r->inflight = true;
     return SCA_OK;
@@ -384,10 +393,13 @@ int sca_server_create(size_t budget_bytes, uint32_t max_active, uint32_t max_L, 
         uint64_t thr = budget_bytes;     // keep freed state memory in the pool up to the budget
         e = cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
+    int prio_least = 0, prio_greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     srv->slots.resize(max_active);
     for (uint32_t i = 0; i < max_active && e == cudaSuccess; ++i) {
         Slot &sl = srv->slots[i];
         e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.stream_hi, cudaStreamNonBlocking, prio_greatest);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.pinned, kResCap * sizeof(sca_obs));
     }
@@ -558,8 +570,11 @@ void sca_server_destroy(sca_server *srv)
     if (srv->worker.joinable()) srv->worker.join();
     for (auto &kv : srv->reqs) delete kv.second;
     for (Slot &sl : srv->slots) {
-        if (sl.stream) cudaStreamSynchronize(sl.stream);
-        if (sl.stream) cudaStreamDestroy(sl.stream);
+        for (cudaStream_t st : {sl.stream, sl.stream_hi}) {
+            if (!st) continue;
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.pinned) cudaFreeHost(sl.pinned);
     }
