@@ -100,6 +100,8 @@ CASES = [
     (1024, 0.6180339887, 0.1, 2, 2, [1, 3]),
     (2048, 0.75, 0.25, 1, 12, [1, 2]),
     (4096, 0.875, 0.125, 1, 3, [1]),
+    (2880, 0.7, 0.3, 2, 21, [1, 2]),                   # W = 45: uniform teams across warps
+    (5120, 0.55, 0.45, 2, 22, [1]),                    # W = 80: 20-thread teams, 240-thread blocks
     (128, 1.0, 1.0, 1, 5, [1, 2, 3]),                  # deterministic both ways
     (128, 0.0, 0.0, 1, 5, [1, 4]),                     # identity
 ]
