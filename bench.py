@@ -427,7 +427,7 @@ def run_batched(sca, torch, stream, dev, L_single, peak):
     sites = sum(d["L"] ** 2 for d in ens)
     with sca.Batch(ens, stream=stream) as b:
         c, t = b.tune(16)
-        b.run(times, want_obs=False)          # warm-up (captures the graph)
+        obs, _ = b.run(times, want_obs=True)  # warm-up (captures the graph); per-class W^2
         b.reset()
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -440,6 +440,12 @@ def run_batched(sca, torch, stream, dev, L_single, peak):
         shape = b.shape()
         engine = b.engine()
     rate = sites * 4096 / (ms / 1000.0)
+    # ensemble-averaged W^2 at the last time per class (lattice size and rule), from the
+    # warm-up run (the timed run repeats it exactly: the same seeds and counters)
+    per_class = {}
+    for d, o in zip(ens, obs):
+        per_class.setdefault("L=%d (%g,%g)" % (d["L"], d["p"], d["q"]), []).append(o[-1].w2)
+    class_w2 = {k: float(np.mean(v)) for k, v in sorted(per_class.items())}
     # single-lattice rates for the same two rules at L = 65536
     single = {}
     for p, q in ((1.0, 0.0), (0.875, 0.125)):
@@ -464,7 +470,7 @@ def run_batched(sca, torch, stream, dev, L_single, peak):
             "ratio_to_single": rate / mix,
             "engine": {1: "clusters (shared memory)", 2: "streaming (register wavefront)"}.get(engine, engine),
             "cluster_shape": shape, "tuned": [c, t],
-            "ensemble_w2_final": w2[-1]}
+            "ensemble_w2_final": w2[-1], "class_w2_final": class_w2}
 
 
 def run_ours(a, rank, world, local_rank):
