@@ -8,6 +8,8 @@
 // into the next word; both go through shared memory with a barrier, as in the paper, but
 // only at team-boundary words (the rest stays in registers).  Rows of one sublattice are
 // independent, so every team works on its own rows in any order.
+#include <atomic>
+
 #include "sca_internal.h"
 
 namespace sca {
@@ -195,35 +197,39 @@ static cudaError_t launch_half_v(const HalfArgs &a, const TeamShape &ts, cudaStr
     return cudaGetLastError();
 }
 
-// Resident blocks per SM of the per-site uniform kernel with V words per thread and 128-thread
-// blocks (asked once per V).
-static int uniform_blocks_per_sm(int V)
+// Resident warps per SM of the per-site uniform kernel with V words per thread (asked once per
+// V with 128-thread blocks; registers bound it, so the count is per warp).
+static int uniform_warps_per_sm(int V)
 {
-    static int cached[5] = {0, 0, 0, 0, 0};
-    if (cached[V] == 0) {
+    static std::atomic<int> cached[3];
+    int w = cached[V].load(std::memory_order_relaxed);
+    if (w == 0) {
         int n = 0;
         cudaError_t e = V == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_half_step<1, 2>, 128, 2 * 4 * 128)
                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_half_step<2, 2>, 128, 2 * 4 * 128);
-        cached[V] = (e == cudaSuccess && n > 0) ? n : 1;
+        w = (e == cudaSuccess && n > 0) ? 4 * n : 4;
+        cached[V].store(w, std::memory_order_relaxed);
     }
-    return cached[V];
+    return w;
 }
 
 // Team shape of a per-site uniform half-step.  Each word costs eight Philox calls, so on a
 // lattice too small to fill the GPU the launch lasts about as long as one thread's chain of
 // calls, and fewer words per thread shorten it.  The fewest words per thread (1, then 2) whose
-// 128-thread blocks still fit within 1.2 resident waves is taken, else the default shape.
+// warps still fit within 1.2 resident waves is taken (blocks of about 128 threads; a row team
+// of more than 512 threads, the kernel's bound, rules a count out), else the default shape.
 // Measured on GB300 (two-pass kernel alone): L = 4096 8.2e11 against 6.8e11 updates/s with
 // four words per thread, L = 2048 3.4e11 against 2.6e11, L = 1024 1.3e11 against 6.4e10;
 // L >= 8192 keeps four words per thread.
 static TeamShape uniform_shape(uint32_t W, uint32_t Y)
 {
     for (int v = 1; v <= 2; ++v) {
-        if (W % (uint32_t)v) continue;
+        if (W % (uint32_t)v || W / (uint32_t)v > 512u) continue;
         const TeamShape ts = team_shape_v(W, v, 128);
         const uint64_t blocks = ((uint64_t)Y + ts.teams - 1) / ts.teams;
-        const uint64_t resident = (uint64_t)sm_count() * (uint64_t)uniform_blocks_per_sm(v);
-        if (5 * blocks <= 6 * resident) return ts;
+        const uint64_t warps = blocks * (uint64_t)((ts.block + 31) / 32);
+        const uint64_t resident = (uint64_t)sm_count() * (uint64_t)uniform_warps_per_sm(v);
+        if (5 * warps <= 6 * resident) return ts;
     }
     return team_shape(W, 256);
 }

@@ -73,6 +73,8 @@ CASES = [
     (64, 2048, 0.5, 0.5, [1, 6]),            # tall and narrow
     (131072, 16, 0.5, 0.0, [1, 3]),          # the paper's wide system, X = 2^17, a few rows
     (320, 96, 0.9, 0.05, [3, 5]),            # per-site uniforms
+    (131072, 16, 0.7, 0.3, [1, 2]),          # per-site uniforms on 2048-word rows, few rows
+    (65536, 8, 0.6, 0.4, [1]),               # per-site uniforms, 512-thread row teams
 ]
 
 
