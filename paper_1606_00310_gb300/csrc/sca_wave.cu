@@ -18,11 +18,16 @@ int wave_uniform_blocks_per_sm(int K);
 // launch streams at memory speed: a tile then owns 120 words, whole 32-byte sectors starting on
 // a sector, so no sector is written by two tiles (with one word per lane the 30-word tiles
 // share edge sectors that L2 evicted half-written and refilled from DRAM: 0.9 GB read per launch
-// at L = 65536 against 0.54 GB), and its loads are 16 bytes a lane.  Else one.
+// at L = 65536 against 0.54 GB), and its loads are 16 bytes a lane.  At 4 MCS per launch on rows
+// of 1024 words or more they take four too (161 registers against 64, but the launch still moves
+// the state once per 4 MCS: 0.17 ms less per benchmark step at L = 65536, whose run to t = 8 is
+// one such launch).  Else one.
 static int wave_V(uint32_t L, int mode, uint32_t k)
 {
     if ((L / 64) % 4 != 0) return 1;
-    return mode == 1 || (mode == 0 && k <= 2) ? 4 : 1;
+    if (mode == 1) return 4;
+    if (mode == 0 && (k <= 2 || (k == 4 && L / 64 >= 1024))) return 4;
+    return 1;
 }
 
 template <int K, int V, bool DP, bool DQ>
@@ -77,7 +82,7 @@ static int blocks_for(int K, int V, const Rule &R, uint32_t X, uint32_t Y)
     switch (K) {
     case 1: return V == 4 ? blocks_mode0<1, 4>(dp, dq) : blocks_mode0<1, 1>(dp, dq);
     case 2: return V == 4 ? blocks_mode0<2, 4>(dp, dq) : blocks_mode0<2, 1>(dp, dq);
-    case 4: return blocks_mode0<4, 1>(dp, dq);
+    case 4: return V == 4 ? blocks_mode0<4, 4>(dp, dq) : blocks_mode0<4, 1>(dp, dq);
     case 8: return blocks_mode0<8, 1>(dp, dq);
     default: return blocks_mode0<16, 1>(dp, dq);
     }
@@ -174,7 +179,7 @@ cudaError_t launch_wave_xy(const uint32_t *src, uint32_t *dst, uint32_t X, uint3
     switch (k) {
     case 1: return V == 4 ? launch_mode0<1, 4>(a, grid, st) : launch_mode0<1, 1>(a, grid, st);
     case 2: return V == 4 ? launch_mode0<2, 4>(a, grid, st) : launch_mode0<2, 1>(a, grid, st);
-    case 4: return launch_mode0<4, 1>(a, grid, st);
+    case 4: return V == 4 ? launch_mode0<4, 4>(a, grid, st) : launch_mode0<4, 1>(a, grid, st);
     case 8: return launch_mode0<8, 1>(a, grid, st);
     case 16: return launch_mode0<16, 1>(a, grid, st);
     default: return cudaErrorInvalidValue;
