@@ -626,22 +626,45 @@ def run_ours(a, rank, world, local_rank):
         sims, outs, streams = [sim, sim2], [host_out, host_out2], [stream, stream2]
 
         def pipelined(k):
-            pending, updated = None, None
+            # events on each step's stream (before the copy in, after it and the surface check,
+            # when the updates start, when they end, after the copy out) and the host time the
+            # run call spends waiting for that check: where a step's time goes
+            pending, updated, rec = None, None, []
             for i in range(k):
-                s = sims[i % 2]
+                s, st_ = sims[i % 2], streams[i % 2]
+                ev = {x: torch.cuda.Event(enable_timing=True) for x in "abce"}
+                ev["a"].record(st_)
                 s.set_state_ptr_async(host_in.data_ptr(), n_words, 0)
+                ev["b"].record(st_)
                 if updated is not None:
-                    streams[i % 2].wait_event(updated)
+                    st_.wait_event(updated)
+                ev["c"].record(st_)
+                h0 = time.perf_counter()
                 s.run_async(times)
-                updated = torch.cuda.Event()
-                updated.record(streams[i % 2])
+                ev["host_run_ms"] = 1e3 * (time.perf_counter() - h0)
+                updated = torch.cuda.Event(enable_timing=True)
+                updated.record(st_)
+                ev["d"] = updated
                 s.get_state_ptr_async(outs[i % 2].data_ptr(), n_words)
+                ev["e"].record(st_)
                 if pending is not None:
                     ob = pending.wait()
                     assert ob[-1].t == a.mcs and all(o_.status == 0 for o_ in ob)
                 pending = s
+                rec.append(ev)
             ob = pending.wait()
             assert ob[-1].t == a.mcs and all(o_.status == 0 for o_ in ob)
+            return rec
+
+        def step_profile(rec):
+            torch.cuda.synchronize(dev)
+            mean = lambda v: float(sum(v) / len(v)) if v else None
+            return {"copy_in_and_check_ms": mean([r["a"].elapsed_time(r["b"]) for r in rec]),
+                    "run_ms": mean([r["c"].elapsed_time(r["d"]) for r in rec]),
+                    "copy_out_ms": mean([r["d"].elapsed_time(r["e"]) for r in rec]),
+                    "gap_between_runs_ms": mean([rec[i - 1]["d"].elapsed_time(rec[i]["c"])
+                                                 for i in range(1, len(rec))]),
+                    "host_run_call_ms": mean([r["host_run_ms"] for r in rec])}
 
         pipelined(2)
         sync_all()
@@ -649,9 +672,10 @@ def run_ours(a, rank, world, local_rank):
         sim2.timing(True)
         clk_e2e = ClockSampler(gpu_index)
         t0 = time.perf_counter()
-        pipelined(a.steps)
+        e2e_rec = pipelined(a.steps)
         sync_all()
         e2e_s = time.perf_counter() - t0
+        e2e_steps = step_profile(e2e_rec)
         clk_e2e = clk_e2e.stop()
         # the updates' own device time inside the pipelined region (CUDA events around each
         # run's update launches): the difference to ms_per_step is what the copies did not hide
@@ -686,7 +710,7 @@ def run_ours(a, rank, world, local_rank):
                "sequential_value": seq_value,
                "sequential_ms_per_step": 1000.0 * seq_s / a.steps,
                "pinned_h2d_GBs": h2d_GBs, "pinned_d2h_GBs": d2h_GBs,
-               "update_ms_per_step": e2e_upd_ms / a.steps,
+               "update_ms_per_step": e2e_upd_ms / a.steps, "step_profile": e2e_steps,
                "clocks": clk_e2e, "clocks_sequential": clk_seq}
 
     # context: the paper's own benchmark case p = 1/2, q = 0 (random bits every update)
