@@ -359,12 +359,15 @@ uint64_t sca_batch_time(const sca_batch *b);
 void sca_batch_free(sca_batch *b);
 
 /* ---- serving: continuous batching of independent simulations -------------------------------
- * A server owns a scheduler thread and up to max_active slots (a stream each).  Requests queue
- * in arrival order and are admitted while a slot is free and the sum of admitted requests'
- * state (sca_workspace_bytes(L) + 256 each) stays within budget_bytes; their memory comes from
- * the device's stream-ordered pool.  Admitted requests run concurrently, each on its own
- * stream, advancing in replayed CUDA graphs of 64 MCS; a request's results equal those of a
- * sca_sim with the same parameters run alone.  Times are seconds since sca_server_create. */
+ * A server owns a scheduler thread and up to max_active slots (two streams each, one at the
+ * device's highest priority).  Requests queue in arrival order and are admitted while a slot is
+ * free and the sum of admitted requests' state (sca_workspace_bytes(L) + 256 each) stays within
+ * budget_bytes; their memory comes from the device's stream-ordered pool.  Admitted requests
+ * run concurrently, each on its own stream, advancing in replayed CUDA graphs of 64 MCS;
+ * requests of at most 2^33 site updates (L * L * n_mcs) take the high-priority stream, so the
+ * GPU starts their blocks first, and per-site uniform requests run the two-pass kernel (the
+ * kernel that shares the GPU best).  A request's results equal those of a sca_sim with the same
+ * parameters run alone, whatever the kernel.  Times are seconds since sca_server_create. */
 typedef struct sca_server sca_server;   /* opaque */
 
 typedef struct sca_request_info {
